@@ -1,0 +1,183 @@
+// Internal declarations of the GB300 ACR library: device buffers, batched
+// HODLR matrix views, the batched GEMM operand descriptor and the launchers.
+//
+// Layout conventions (all per plane, planes of one batch at a fixed stride):
+//   * a plane's n^2 unknowns are permuted so every cluster of the 2D bisection
+//     tree (Section 3.1) is a contiguous index range; the level-l clusters
+//     (l = 1..L) have size m >> l, the leaves have size b = m >> L;
+//   * HODLR leaves: 2^L dense b x b blocks, row major, leaf-major;
+//   * HODLR level l (l = 0..L-1): two row-major m x K_l panels U_l, V_l.
+//     For the level-(l+1) cluster c and its sibling c^1 the off-diagonal block
+//     M[c, c^1] = U_l|c * (V_l|c^1)^T  (rows of c in U, rows of c^1 in V);
+//     columns beyond a block's rank are zero.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <map>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+namespace acr {
+
+constexpr int MAXL = 16;
+
+struct AcrError : std::runtime_error {
+  int code;
+  AcrError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define ACR_CUDA(x)                                                                      \
+  do {                                                                                   \
+    cudaError_t e_ = (x);                                                                \
+    if (e_ != cudaSuccess) {                                                             \
+      if (e_ == cudaErrorMemoryAllocation) throw ::acr::AcrError(2, cudaGetErrorString(e_)); \
+      throw ::acr::AcrError(5, std::string(#x) + ": " + cudaGetErrorString(e_));         \
+    }                                                                                    \
+  } while (0)
+
+// Execution context of one handle: stream, scratch, counters, autotune cache.
+struct Ctx {
+  cudaStream_t st = nullptr;
+  int* d_flag = nullptr;            // device status flags (breakdown ...)
+  long long launches = 0;
+  long long gemm_flops = 0;
+  size_t live_bytes = 0, peak_bytes = 0, budget = 0;
+  bool autotune = false;
+  std::vector<std::pair<unsigned long long, int>> tuned;  // shape key -> config
+  std::map<uintptr_t, size_t> live;  // allocation start -> bytes (for the operand extent check)
+  bool check_bounds = false;         // ACR_CHECK_BOUNDS=1: verify every GEMM operand range on the host
+  void check_range(const void* base, long lo, long hi, size_t es, const char* what) const;
+  void* dalloc_bytes(size_t bytes);
+  void dfree(void* p, size_t bytes);
+  template <class T> T* alloc(size_t n) { return static_cast<T*>(dalloc_bytes(n * sizeof(T))); }
+  template <class T> void free(T* p, size_t n) { dfree(p, n * sizeof(T)); }
+};
+
+// Owned device buffer with size bookkeeping.
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  Ctx* c = nullptr;
+  DBuf() = default;
+  DBuf(Ctx& ctx, size_t cnt, bool zero = false);
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { *this = std::move(o); }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; c = o.c; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void release();
+};
+
+// Batched GEMM operand: element (i, j) of batch entry (plane, cluster c) is
+//   p[plane*ps + (cc >> sh)*c1 + (cc & 1)*c2 + i*rs + j*cs],  cc = sib ? c^1 : c.
+template <class T>
+struct Op {
+  T* p = nullptr;
+  long rs = 0, cs = 0, ps = 0, c1 = 0, c2 = 0;
+  int sh = 0, sib = 0;
+};
+
+// C = alpha * A(MxK) * B(KxN) + beta * C over nplanes x nclus batch entries.
+template <class T>
+void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta,
+          Op<T> C);
+
+// Panel view: rows m per plane, element (row, col) at p[plane*ps + row*ld + col].
+template <class T>
+struct Pan {
+  T* p = nullptr;
+  long ld = 0, ps = 0;
+};
+
+// View of P HODLR matrices (planes at stride lps / pps[l]).
+template <class T>
+struct HMat {
+  int P = 0, m = 0, L = 0, b = 0;
+  T* leaf = nullptr;
+  long lps = 0;
+  T* U[MAXL] = {};
+  T* V[MAXL] = {};
+  int K[MAXL] = {};
+  long pps[MAXL] = {};
+  HMat sub(int p0, int step, int count) const {
+    HMat r = *this;
+    r.P = count;
+    r.leaf = leaf + (long)p0 * lps;
+    r.lps = lps * step;
+    for (int l = 0; l < L; ++l) {
+      if (U[l]) { r.U[l] = U[l] + (long)p0 * pps[l]; r.V[l] = V[l] + (long)p0 * pps[l]; }
+      r.pps[l] = pps[l] * step;
+    }
+    return r;
+  }
+  long bytes() const {
+    long s = (long)P * m * b;
+    for (int l = 0; l < L; ++l) s += 2L * P * m * K[l];
+    return s * (long)sizeof(T);
+  }
+};
+
+// Owner of a contiguous batch of HODLR matrices.
+template <class T>
+struct HStore {
+  DBuf<T> leaf;
+  DBuf<T> U[MAXL], V[MAXL];
+  HMat<T> h;
+  HStore() = default;
+  HStore(HStore&&) = default;
+  HStore& operator=(HStore&&) = default;
+};
+
+// Planner output (host): cluster tree of one n x n plane.
+struct Geometry {
+  int n = 0, m = 0, leaf = 0, L = 0;
+  std::vector<int> perm;              // permuted position -> lexicographic in-plane index
+  std::vector<int> ncut;              // per level: cut edges per node
+  std::vector<std::vector<int>> cutp, cutq;  // per level: [node*ncut + e] positions
+};
+int plan_geometry(int n, int leaf, Geometry& g);  // 0 or ACR_ERR_ARG
+
+// ---- small kernels (small_kernels.cu) -------------------------------------
+template <class T> void fill(Ctx& c, T* p, long n, T v);
+template <class T> void copy2d(Ctx& c, int P, long rows, int cols, T alpha, const T* src, long sld,
+                               long sps, T* dst, long dld, long dps);
+template <class T> void set_identity_clusters(Ctx& c, int P, int m, int s, T* U, long ld, long ps);
+template <class T> int batched_inverse(Ctx& c, int nb, int n, T* A, long stride);  // in place GJ, returns 0
+template <class T> void build_coupling(Ctx& c, int P, int nodes, int K, const T* g, T* Mout);
+template <class T> void assemble_level0(Ctx& c, const Geometry& geo, const double* kappa, double shift,
+                                        const int* d_perm, const int* d_iperm,
+                                        const std::vector<const int*>& d_cutp,
+                                        const std::vector<const int*>& d_cutq, HMat<T> D, HMat<T> E,
+                                        HMat<T> F);
+template <class T> void permute_in(Ctx& c, int n, int nrhs, const double* b, long ld, const int* d_perm,
+                                   T* F);
+template <class T> void permute_out(Ctx& c, int n, int nrhs, const T* F, const int* d_perm, double* x,
+                                    long ld, int accumulate);
+void stencil_apply(Ctx& c, int n, int nrhs, const double* coef, const double* x, long ld, const double* y,
+                   double* out, double alpha, double beta, double* norms_out /*2*nrhs or null*/);
+template <class T> void expand_leaves(Ctx& c, int m, int b, const T* leaf, T* dense);
+void exp_inplace(Ctx& c, double* p, long n);
+void face_coefficients(Ctx& c, int n, const double* kappa, double shift, double* coef);
+void col_dots(Ctx& c, long N, int nrhs, const double* x, long ldx, const double* y, long ldy, double* out);
+void col_axpy(Ctx& c, long N, int nrhs, const double* a /*device nrhs*/, const double* x, long ldx,
+              double* y, long ldy);
+void col_scale_copy(Ctx& c, long N, int nrhs, const double* a, const double* x, long ldx, double* y,
+                    long ldy);
+
+// ---- recompression (recompress.cu) ----------------------------------------
+// Level-l recompression of the off-diagonal blocks  Left|c * Right|c^1 ^T  for
+// every level-(l+1) cluster c of P planes.  Left/Right are [P][m][r] row
+// major (ld r) and are consumed (freed or adopted).  Output panels have
+// capacity *Kout.  tol < 0 (or exact) keeps blocks exact.
+template <class T>
+void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& Right, int r, double tol,
+                      bool exact, DBuf<T>& Uout, DBuf<T>& Vout, int& Kout);
+
+}  // namespace acr

@@ -1,0 +1,323 @@
+// Batched strided GEMM for the HODLR arithmetic: C = alpha A B + beta C over
+// (plane, cluster) batch entries whose operands are located by Op<T>.
+//
+// Every product the H-arithmetic needs (leaf products, V^T W coefficient
+// reductions over a cluster, U T expansions, Gram matrices, rebuilds) is one
+// call.  Tall reductions with few batch entries are split along K into a
+// scratch buffer and reduced by a second kernel.  Four register tilings exist;
+// with autotuning enabled the fastest one per (precision, shape class) is
+// measured once with CUDA events and cached for the process.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "acr_internal.h"
+
+namespace acr {
+
+template <class T>
+struct GArgs {
+  int M, N, K, nclus, batch;
+  T alpha, beta;
+  Op<T> A, B, C;
+  int kchunk;
+  T* partial;
+};
+
+template <class T>
+__device__ __forceinline__ T* opaddr(const Op<T>& o, int plane, int c) {
+  int cc = o.sib ? (c ^ 1) : c;
+  return o.p + (long)plane * o.ps + (long)(cc >> o.sh) * o.c1 + (long)(cc & 1) * o.c2;
+}
+
+template <class T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GArgs<T> g) {
+  constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
+  __shared__ T As[BK][BM + 4];
+  __shared__ T Bs[BK][BN + 4];
+  const int bi = blockIdx.x;
+  const int plane = bi / g.nclus, c = bi - plane * g.nclus;
+  const int tilesN = (g.N + BN - 1) / BN;
+  const int m0 = (blockIdx.y / tilesN) * BM, n0 = (blockIdx.y % tilesN) * BN;
+  const int kbeg = blockIdx.z * g.kchunk;
+  const int kend = min(g.K, kbeg + g.kchunk);
+  const T* __restrict__ A = opaddr(g.A, plane, c);
+  const T* __restrict__ B = opaddr(g.B, plane, c);
+  const long ars = g.A.rs, acs = g.A.cs, brs = g.B.rs, bcs = g.B.cs;
+  const int tid = threadIdx.x, tx = tid % NTX, ty = tid / NTX;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  const bool a_kfast = (acs == 1), b_nfast = (bcs == 1);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    if (a_kfast) {
+      for (int e = tid; e < BM * BK; e += NT) {
+        int ii = e / BK, kk = e % BK;
+        int gi = m0 + ii, gk = k0 + kk;
+        As[kk][ii] = (gi < g.M && gk < kend) ? A[(long)gi * ars + gk] : T(0);
+      }
+    } else {
+      for (int e = tid; e < BM * BK; e += NT) {
+        int ii = e % BM, kk = e / BM;
+        int gi = m0 + ii, gk = k0 + kk;
+        As[kk][ii] = (gi < g.M && gk < kend) ? A[(long)gi * ars + (long)gk * acs] : T(0);
+      }
+    }
+    if (b_nfast) {
+      for (int e = tid; e < BK * BN; e += NT) {
+        int kk = e / BN, jj = e % BN;
+        int gk = k0 + kk, gj = n0 + jj;
+        Bs[kk][jj] = (gk < kend && gj < g.N) ? B[(long)gk * brs + gj] : T(0);
+      }
+    } else {
+      for (int e = tid; e < BK * BN; e += NT) {
+        int kk = e % BK, jj = e / BK;
+        int gk = k0 + kk, gj = n0 + jj;
+        Bs[kk][jj] = (gk < kend && gj < g.N) ? B[(long)gk * brs + (long)gj * bcs] : T(0);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  if (g.partial) {
+    T* P = g.partial + ((long)blockIdx.z * g.batch + bi) * (long)g.M * g.N;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      int gi = m0 + ty * TM + i;
+      if (gi >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        int gj = n0 + tx * TN + j;
+        if (gj < g.N) P[(long)gi * g.N + gj] = acc[i][j];
+      }
+    }
+    return;
+  }
+  T* C = opaddr(g.C, plane, c);
+  const long crs = g.C.rs, ccs = g.C.cs;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int gi = m0 + ty * TM + i;
+    if (gi >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int gj = n0 + tx * TN + j;
+      if (gj >= g.N) continue;
+      T* cp = C + (long)gi * crs + (long)gj * ccs;
+      T v = g.alpha * acc[i][j];
+      if (g.beta != T(0)) v += g.beta * *cp;
+      *cp = v;
+    }
+  }
+}
+
+template <class T>
+__global__ void k_splitk_reduce(GArgs<T> g, int nsplit) {
+  long tot = (long)g.batch * g.M * g.N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    long bi = e / ((long)g.M * g.N);
+    long r = e - bi * (long)g.M * g.N;
+    int i = (int)(r / g.N), j = (int)(r % g.N);
+    T s = T(0);
+    for (int q = 0; q < nsplit; ++q) s += g.partial[((long)q * g.batch + bi) * (long)g.M * g.N + r];
+    int plane = (int)(bi / g.nclus), c = (int)(bi - (long)plane * g.nclus);
+    T* cp = opaddr(g.C, plane, c) + (long)i * g.C.rs + (long)j * g.C.cs;
+    T v = g.alpha * s;
+    if (g.beta != T(0)) v += g.beta * *cp;
+    *cp = v;
+  }
+}
+
+template <class T>
+__global__ void k_scale_c(GArgs<T> g) {
+  long tot = (long)g.batch * g.M * g.N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    long bi = e / ((long)g.M * g.N);
+    long r = e - bi * (long)g.M * g.N;
+    int i = (int)(r / g.N), j = (int)(r % g.N);
+    int plane = (int)(bi / g.nclus), c = (int)(bi - (long)plane * g.nclus);
+    T* cp = opaddr(g.C, plane, c) + (long)i * g.C.rs + (long)j * g.C.cs;
+    *cp = (g.beta == T(0)) ? T(0) : g.beta * *cp;
+  }
+}
+
+namespace {
+
+struct Cfg {
+  int bm, bn, bk;
+};
+constexpr Cfg kCfg[4] = {{64, 64, 16}, {128, 64, 8}, {32, 32, 32}, {128, 128, 8}};
+
+template <class T>
+void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st) {
+  switch (cfg) {
+    case 0: k_gemm<T, 64, 64, 16, 4, 4><<<grid, 256, 0, st>>>(g); break;
+    case 1: k_gemm<T, 128, 64, 8, 8, 4><<<grid, 256, 0, st>>>(g); break;
+    case 2: k_gemm<T, 32, 32, 32, 2, 2><<<grid, 256, 0, st>>>(g); break;
+    default: k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g); break;
+  }
+}
+
+int heuristic_cfg(int M, int N, long batch) {
+  if (M <= 32 && N <= 32) return 2;
+  if (M >= 128 && N >= 128 && batch * ((M + 127) / 128) * ((N + 127) / 128) >= 2 * 152) return 3;
+  if (M >= 128 && N <= 64) return 1;
+  return 0;
+}
+
+int split_for(int cfg, int M, int N, int K, long batch) {
+  long tiles = batch * ((M + kCfg[cfg].bm - 1) / kCfg[cfg].bm) * ((N + kCfg[cfg].bn - 1) / kCfg[cfg].bn);
+  if (tiles >= 2 * 152 || K < 512) return 1;
+  long want = (4 * 152 + tiles - 1) / tiles;
+  long maxs = K / 256;
+  return (int)std::max(1L, std::min({want, maxs, 64L}));
+}
+
+std::mutex g_tune_mu;
+std::vector<std::pair<unsigned long long, int>> g_tuned;
+
+unsigned long long shape_key(int es, int M, int N, int K, long batch) {
+  auto lg = [](long v) { int b = 0; while (v > 1) { v >>= 1; ++b; } return (unsigned long long)b; };
+  return (unsigned long long)es | (lg(M) << 8) | (lg(N) << 16) | (lg(K) << 24) | (lg(batch) << 32);
+}
+
+}  // namespace
+
+template <class T>
+static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch, GArgs<T> g) {
+  const Cfg& f = kCfg[cfg];
+  int tiles = ((M + f.bm - 1) / f.bm) * ((N + f.bn - 1) / f.bn);
+  if (split > 1) {
+    int kchunk = (K + split - 1) / split;
+    kchunk = (kchunk + f.bk - 1) / f.bk * f.bk;
+    split = (K + kchunk - 1) / kchunk;
+    size_t pn = (size_t)split * batch * M * N;
+    T* part = c.alloc<T>(pn);
+    g.kchunk = kchunk;
+    g.partial = part;
+    launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, split), g, c.st);
+    long tot = batch * (long)M * N;
+    int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
+    k_splitk_reduce<T><<<nb, 256, 0, c.st>>>(g, split);
+    c.launches += 2;
+    c.free(part, pn);
+  } else {
+    g.kchunk = K;
+    g.partial = nullptr;
+    launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, 1), g, c.st);
+    c.launches += 1;
+  }
+}
+
+// Host check of the element range an operand touches over all batch entries.
+template <class T>
+static void check_op(const Ctx& c, const Op<T>& o, int nplanes, int nclus, int rows, int cols, const char* what) {
+  if (rows <= 0 || cols <= 0) return;
+  long lo = 0, hi = 0;
+  bool first = true;
+  int cs[4] = {0, 1, nclus - 2, nclus - 1};
+  for (int pp : {0, nplanes - 1})
+    for (int ci : cs) {
+      if (ci < 0 || ci >= nclus) continue;
+      int cc = o.sib ? (ci ^ 1) : ci;
+      long off = (long)pp * o.ps + (long)(cc >> o.sh) * o.c1 + (long)(cc & 1) * o.c2;
+      long top = off + (long)(rows - 1) * o.rs + (long)(cols - 1) * o.cs;
+      long bot = off + std::min(0L, (long)(rows - 1) * o.rs) + std::min(0L, (long)(cols - 1) * o.cs);
+      if (first || bot < lo) lo = bot;
+      if (first || top > hi) hi = top;
+      first = false;
+    }
+  c.check_range(o.p, lo, hi, sizeof(T), what);
+}
+
+template <class T>
+void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta, Op<T> C) {
+  long batch = (long)nplanes * nclus;
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  if (c.check_bounds) {
+    if (K > 0) {
+      check_op(c, A, nplanes, nclus, M, K, "gemm A");
+      check_op(c, B, nplanes, nclus, K, N, "gemm B");
+    }
+    check_op(c, C, nplanes, nclus, M, N, "gemm C");
+  }
+  if (K <= 0) {
+    // Empty inner dimension: C = beta * C.
+    GArgs<T> g{M, N, 0, nclus, (int)batch, T(0), beta, A, B, C, 0, nullptr};
+    long tot = batch * (long)M * N;
+    int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
+    k_scale_c<T><<<nb, 256, 0, c.st>>>(g);
+    c.launches += 1;
+    return;
+  }
+  if (batch > 0x7fffffffL) throw AcrError(1, "gemm batch too large");
+  c.gemm_flops += 2LL * M * N * K * batch;
+  GArgs<T> g{M, N, K, nclus, (int)batch, alpha, beta, A, B, C, K, nullptr};
+  int cfg = heuristic_cfg(M, N, batch);
+  int split = split_for(cfg, M, N, K, batch);
+  if (c.autotune) {
+    unsigned long long key = shape_key(sizeof(T), M, N, K, batch);
+    int found = -1;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      for (auto& kv : g_tuned)
+        if (kv.first == key) { found = kv.second; break; }
+    }
+    if (found < 0) {
+      // Time every candidate writing into a scratch C (beta = 0), keep the fastest.
+      size_t cn = (size_t)batch * M * N;
+      T* cs = c.alloc<T>(cn);
+      GArgs<T> gt = g;
+      gt.beta = T(0);
+      gt.C.p = cs; gt.C.rs = N; gt.C.cs = 1; gt.C.ps = (long)nclus * M * N; gt.C.c1 = (long)M * N;
+      gt.C.c2 = 0; gt.C.sh = 0; gt.C.sib = 0;
+      cudaEvent_t e0, e1;
+      ACR_CUDA(cudaEventCreate(&e0));
+      ACR_CUDA(cudaEventCreate(&e1));
+      float best = 1e30f;
+      int bestc = 0;
+      for (int cand = 0; cand < 8; ++cand) {
+        int cf = cand & 3;
+        int sp = (cand >> 2) ? split_for(cf, M, N, K, batch) : 1;
+        if ((cand >> 2) && sp == 1) continue;
+        run_gemm<T>(c, cf, sp, M, N, K, batch, gt);  // warm
+        ACR_CUDA(cudaEventRecord(e0, c.st));
+        run_gemm<T>(c, cf, sp, M, N, K, batch, gt);
+        ACR_CUDA(cudaEventRecord(e1, c.st));
+        ACR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        ACR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; bestc = cand; }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      c.free(cs, cn);
+      found = bestc;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned.push_back({key, found});
+    }
+    cfg = found & 3;
+    split = (found >> 2) ? split_for(cfg, M, N, K, batch) : 1;
+  }
+  run_gemm<T>(c, cfg, split, M, N, K, batch, g);
+}
+
+template void gemm<float>(Ctx&, int, int, int, int, int, float, Op<float>, Op<float>, float, Op<float>);
+template void gemm<double>(Ctx&, int, int, int, int, int, double, Op<double>, Op<double>, double,
+                           Op<double>);
+
+}  // namespace acr

@@ -1,0 +1,453 @@
+// Batched QR + SVD recompression of low-rank blocks (Section 2.1: every
+// low-rank block is an outer product A B^T kept to a relative accuracy by SVD
+// truncation; Section 3.1: the tolerance is enforced in every H-operation).
+//
+// For a block  M = L R^T  (L: s x r rows of cluster c, R: s x r rows of c^1):
+//   1. orthogonalise both factors, L = Q_L R_L, R = Q_R R_R:
+//        s <= 128  Householder QR of the whole factor in shared memory;
+//        s >  128  Gram matrix (batched GEMM) + pivoted Cholesky, so that
+//                  Q = L[:, piv] R11^{-1} is never formed;
+//   2. core C = R_L R_R^T (r x r), one-sided (Hestenes) Jacobi SVD C = X S Y^T;
+//   3. keep the k singular values > tol * sigma_1;
+//   4. U = Q_L X_k S_k^{1/2},  V = Q_R Y_k S_k^{1/2}  (one GEMM each).
+// When r exceeds the block size s the block is first made explicit (U = I,
+// V = R L^T), which is exact.
+#include <algorithm>
+#include <cmath>
+
+#include "acr_internal.h"
+
+namespace acr {
+
+namespace {
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <class T>
+__device__ T block_sum(T v, T* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  T t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : T(0);
+  if (w == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  T r = red[0];
+  __syncthreads();
+  return r;
+}
+}  // namespace
+
+// ---- Householder QR of an s x r factor (r <= s <= 128) ----------------------
+// Segment j of 2*NB: side = j / NB (0: rows c of L, 1: rows c^1 of R) of block
+// bi = j % NB.  Q (s x r) overwrites the factor, R (r x r) goes to Rout.
+template <class T>
+__global__ void __launch_bounds__(256) k_qr_small(int s, int r, int nclus, long NB, long mr, T* Lp, T* Rp,
+                                                  T* Rout, int* piv, int* kk) {
+  extern __shared__ unsigned char smraw[];
+  T* A = reinterpret_cast<T*>(smraw);  // column major s x r
+  T* tau = A + (long)s * r;
+  __shared__ T red[32];
+  const long j = blockIdx.x;
+  const int side = (int)(j / NB);
+  const long bi = j % NB;
+  const long plane = bi / nclus;
+  const int c = (int)(bi % nclus);
+  const int cl = side ? (c ^ 1) : c;
+  T* src = (side ? Rp : Lp) + plane * mr + (long)cl * s * r;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (long e = tid; e < (long)s * r; e += blockDim.x) {
+    int row = (int)(e / r), col = (int)(e % r);
+    A[(long)col * s + row] = src[e];
+  }
+  __syncthreads();
+  for (int q = 0; q < r; ++q) {
+    T part = T(0);
+    for (int i = q + 1 + tid; i < s; i += blockDim.x) part += A[(long)q * s + i] * A[(long)q * s + i];
+    T xn2 = block_sum(part, red);
+    T x0 = A[(long)q * s + q];
+    T t = T(0), beta = x0, scal = T(0);
+    if (xn2 > T(0)) {
+      beta = -copysign(sqrt(x0 * x0 + xn2), x0);
+      t = (beta - x0) / beta;
+      scal = T(1) / (x0 - beta);
+    }
+    __syncthreads();
+    for (int i = q + 1 + tid; i < s; i += blockDim.x) A[(long)q * s + i] *= scal;
+    if (tid == 0) { tau[q] = t; A[(long)q * s + q] = beta; }
+    __syncthreads();
+    if (t != T(0)) {
+      for (int k = q + 1 + warp; k < r; k += nw) {
+        T w = (lane == 0) ? A[(long)k * s + q] : T(0);
+        for (int i = q + 1 + lane; i < s; i += 32) w += A[(long)q * s + i] * A[(long)k * s + i];
+        w = warp_sum(w) * t;
+        if (lane == 0) A[(long)k * s + q] -= w;
+        for (int i = q + 1 + lane; i < s; i += 32) A[(long)k * s + i] -= w * A[(long)q * s + i];
+      }
+    }
+    __syncthreads();
+  }
+  T* R = Rout + j * (long)r * r;
+  for (long e = tid; e < (long)r * r; e += blockDim.x) {
+    int row = (int)(e / r), col = (int)(e % r);
+    R[e] = (row <= col) ? A[(long)col * s + row] : T(0);
+  }
+  for (int i = tid; i < r; i += blockDim.x) piv[j * r + i] = i;
+  if (tid == 0) kk[j] = r;
+  __syncthreads();
+  // Form Q = H_0 ... H_{r-1} [I; 0] in place (backward accumulation).
+  for (int q = r - 1; q >= 0; --q) {
+    const T t = tau[q];
+    if (q < r - 1) {
+      if (tid == 0) A[(long)q * s + q] = T(1);
+      __syncthreads();
+      for (int k = q + 1 + warp; k < r; k += nw) {
+        T w = T(0);
+        for (int i = q + lane; i < s; i += 32) w += A[(long)q * s + i] * A[(long)k * s + i];
+        w = warp_sum(w) * t;
+        for (int i = q + lane; i < s; i += 32) A[(long)k * s + i] -= w * A[(long)q * s + i];
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < s; i += blockDim.x) {
+      if (i > q) A[(long)q * s + i] *= -t;
+      else if (i < q) A[(long)q * s + i] = T(0);
+    }
+    if (tid == 0) A[(long)q * s + q] = T(1) - t;
+    __syncthreads();
+  }
+  for (long e = tid; e < (long)s * r; e += blockDim.x) {
+    int row = (int)(e / r), col = (int)(e % r);
+    src[e] = A[(long)col * s + row];
+  }
+}
+
+// ---- pivoted Cholesky of a Gram matrix --------------------------------------
+// G (r x r, symmetric PSD) ~ P R^T R P^T; R rows t < kk are valid (original
+// column order, zero in already chosen columns), the rest zero.  Stops when
+// the largest remaining diagonal is <= eps * (largest initial diagonal).
+template <class T>
+__global__ void __launch_bounds__(256) k_pchol(int r, const T* Gall, T eps, T* Rall, int* pivall, int* kkall) {
+  extern __shared__ unsigned char smraw[];
+  T* d = reinterpret_cast<T*>(smraw);
+  __shared__ T rv[256];
+  __shared__ int ri[256];
+  __shared__ T s_dmax0;
+  const long j = blockIdx.x;
+  const T* G = Gall + j * (long)r * r;
+  T* R = Rall + j * (long)r * r;
+  int* piv = pivall + j * r;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < r; i += blockDim.x) d[i] = fmax(G[(long)i * r + i], T(0));
+  __syncthreads();
+  int t = 0;
+  for (; t < r; ++t) {
+    T best = T(-1);
+    int bi = 0;
+    for (int i = tid; i < r; i += blockDim.x)
+      if (d[i] > best) { best = d[i]; bi = i; }
+    rv[tid] = best;
+    ri[tid] = bi;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+      if (tid < st && (rv[tid + st] > rv[tid] || (rv[tid + st] == rv[tid] && ri[tid + st] < ri[tid]))) {
+        rv[tid] = rv[tid + st];
+        ri[tid] = ri[tid + st];
+      }
+      __syncthreads();
+    }
+    const T dp = rv[0];
+    const int p = ri[0];
+    if (t == 0 && tid == 0) s_dmax0 = dp;
+    __syncthreads();
+    if (!(dp > eps * s_dmax0) || !(dp > T(0))) break;
+    const T sq = sqrt(dp), isq = T(1) / sq;
+    for (int i = tid; i < r; i += blockDim.x) {
+      T v;
+      if (d[i] < T(0)) {
+        v = T(0);  // already chosen column
+      } else if (i == p) {
+        v = sq;
+      } else {
+        v = G[(long)p * r + i];
+        for (int u = 0; u < t; ++u) v -= R[(long)u * r + p] * R[(long)u * r + i];
+        v *= isq;
+      }
+      R[(long)t * r + i] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < r; i += blockDim.x) {
+      if (i == p) d[i] = T(-1);
+      else if (d[i] >= T(0)) d[i] = fmax(d[i] - R[(long)t * r + i] * R[(long)t * r + i], T(0));
+    }
+    if (tid == 0) piv[t] = p;
+    __syncthreads();
+  }
+  for (long e = (long)t * r + tid; e < (long)r * r; e += blockDim.x) R[e] = T(0);
+  if (tid == 0) kkall[j] = t;
+}
+
+// ---- one-sided Jacobi SVD of the core ----------------------------------------
+// C (row major, valid kL x kR) = X diag(sig) Y^T, sig sorted descending.
+// X[i][t] (i < kL) and Y[i][t] (i < kR) row major with leading dimension r;
+// rank = #{sig > tol sig_1}.
+template <class T>
+__global__ void __launch_bounds__(256) k_jacobi(int r, const T* Call, const int* kk, long NB, T* Wall, T* Vall,
+                                                T* Xall, T* Yall, T* sigall, int* rankall, T tol, int maxsweeps) {
+  extern __shared__ unsigned char smraw[];
+  T* sig = reinterpret_cast<T*>(smraw);
+  int* ord = reinterpret_cast<int*>(sig + r);
+  __shared__ int s_rot;
+  __shared__ T red[32];
+  const long bi = blockIdx.x;
+  const T* C = Call + bi * (long)r * r;
+  T* W = Wall + bi * (long)r * r;  // column major, ld r
+  T* V = Vall + bi * (long)r * r;
+  const int kL = kk[bi], kR = kk[NB + bi];
+  const int trans = kL < kR;
+  const int nrow = trans ? kR : kL, ncol = trans ? kL : kR;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const T eps = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
+  if (ncol == 0) {
+    if (tid == 0) rankall[bi] = 0;
+    for (int i = tid; i < r; i += blockDim.x) sigall[bi * r + i] = T(0);
+    return;
+  }
+  for (long e = tid; e < (long)nrow * ncol; e += blockDim.x) {
+    int row = (int)(e % nrow), col = (int)(e / nrow);
+    W[(long)col * r + row] = trans ? C[(long)col * r + row] : C[(long)row * r + col];
+  }
+  for (long e = tid; e < (long)ncol * ncol; e += blockDim.x) {
+    int row = (int)(e % ncol), col = (int)(e / ncol);
+    V[(long)col * r + row] = (row == col) ? T(1) : T(0);
+  }
+  __syncthreads();
+  const int ne = ncol + (ncol & 1);
+  for (int sw = 0; sw < maxsweeps && ne > 1; ++sw) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int step = 0; step < ne - 1; ++step) {
+      for (int k = warp; k < ne / 2; k += nw) {
+        int i, jx;
+        if (k == 0) {
+          i = 0;
+          jx = 1 + step % (ne - 1);
+        } else {
+          i = 1 + (step + k) % (ne - 1);
+          jx = 1 + ((step - k) % (ne - 1) + (ne - 1)) % (ne - 1);
+        }
+        if (i >= ncol || jx >= ncol) continue;
+        T* wi = W + (long)i * r;
+        T* wj = W + (long)jx * r;
+        T a = 0, b = 0, g = 0;
+        for (int q = lane; q < nrow; q += 32) {
+          T x = wi[q], y = wj[q];
+          a += x * x;
+          b += y * y;
+          g += x * y;
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (g != T(0) && fabs(g) > eps * sqrt(a * b)) {
+          T zeta = (b - a) / (T(2) * g);
+          T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+          for (int q = lane; q < nrow; q += 32) {
+            T x = wi[q], y = wj[q];
+            wi[q] = cs * x - sn * y;
+            wj[q] = sn * x + cs * y;
+          }
+          T* vi = V + (long)i * r;
+          T* vj = V + (long)jx * r;
+          for (int q = lane; q < ncol; q += 32) {
+            T x = vi[q], y = vj[q];
+            vi[q] = cs * x - sn * y;
+            vj[q] = sn * x + cs * y;
+          }
+          if (lane == 0) s_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int rot = s_rot;
+    __syncthreads();
+    if (!rot) break;
+  }
+  for (int col = warp; col < ncol; col += nw) {
+    T a = 0;
+    for (int q = lane; q < nrow; q += 32) a += W[(long)col * r + q] * W[(long)col * r + q];
+    a = warp_sum(a);
+    if (lane == 0) sig[col] = sqrt(a);
+  }
+  __syncthreads();
+  for (int col = tid; col < ncol; col += blockDim.x) {
+    int pos = 0;
+    T v = sig[col];
+    for (int o = 0; o < ncol; ++o) pos += (sig[o] > v) || (sig[o] == v && o < col);
+    ord[pos] = col;
+  }
+  __syncthreads();
+  T smax = sig[ord[0]];
+  int rank = 0;
+  if (smax > T(0)) {
+    T thr = fmax(tol * smax, smax * eps * T(4));
+    for (int t = 0; t < ncol; ++t) rank += sig[ord[t]] > thr;
+  }
+  T* X = Xall + bi * (long)r * r;
+  T* Y = Yall + bi * (long)r * r;
+  for (long e = tid; e < (long)rank * r; e += blockDim.x) {
+    int t = (int)(e / r), i = (int)(e % r);
+    int col = ord[t];
+    T sc = sig[col];
+    T wv = (i < nrow) ? W[(long)col * r + i] / sc : T(0);
+    T vv = (i < ncol) ? V[(long)col * r + i] : T(0);
+    // !trans: X = W/s (kL = nrow rows), Y = V (kR = ncol rows); trans: swapped.
+    X[(long)i * r + t] = trans ? vv : wv;
+    Y[(long)i * r + t] = trans ? wv : vv;
+  }
+  for (int i = tid; i < r; i += blockDim.x) sigall[bi * r + i] = (i < ncol) ? sig[ord[i]] : T(0);
+  if (tid == 0) rankall[bi] = rank;
+}
+
+// ---- coefficients of the rebuild ---------------------------------------------
+// Z (r x Kout, row major) per side of block bi such that the new factor is
+// factor * Z:  QR path  Z[0:k, t] = X[:, t] sqrt(s_t);  Gram path  Z[piv[u], t] = z[u],
+// R11 z = X[:, t] sqrt(s_t)  with R11[u][v] = R[u][piv[v]] (upper triangular).
+template <class T>
+__global__ void __launch_bounds__(256) k_coef(int r, int Kout, long NB, int qr, const T* Rall, const int* pivall,
+                                              const int* kkall, const T* Xall, const T* Yall, const T* sigall,
+                                              const int* rankall, T* Zall) {
+  const long j = blockIdx.x;
+  const int side = (int)(j / NB);
+  const long bi = j % NB;
+  const T* R = Rall + j * (long)r * r;
+  const int* piv = pivall + j * r;
+  const int k = kkall[j];
+  const T* XY = (side ? Yall : Xall) + bi * (long)r * r;
+  const T* sig = sigall + bi * r;
+  const int rank = rankall[bi];
+  T* Z = Zall + j * (long)r * Kout;
+  for (long e = threadIdx.x; e < (long)r * Kout; e += blockDim.x) Z[e] = T(0);
+  __syncthreads();
+  for (int t = threadIdx.x; t < rank; t += blockDim.x) {
+    const T sq = sqrt(sig[t]);
+    if (qr) {
+      for (int u = 0; u < k; ++u) Z[(long)u * Kout + t] = XY[(long)u * r + t] * sq;
+    } else {
+      for (int u = k - 1; u >= 0; --u) {
+        T v = XY[(long)u * r + t] * sq;
+        for (int w = u + 1; w < k; ++w) v -= R[(long)u * r + piv[w]] * Z[(long)piv[w] * Kout + t];
+        Z[(long)piv[u] * Kout + t] = v / R[(long)u * r + piv[u]];
+      }
+    }
+  }
+}
+
+template <class T>
+void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& Right, int r, double tol, bool exact,
+                      DBuf<T>& Uout, DBuf<T>& Vout, int& Kout) {
+  const int s = m >> (lvl + 1);
+  const int nclus = 1 << (lvl + 1);
+  const long NB = (long)P * nclus;
+  DBuf<T> Lb = std::move(Left), Rb = std::move(Right);
+  if (r <= 0) {
+    Kout = 0;
+    Uout.release();
+    Vout.release();
+    return;
+  }
+  if (r > s) {
+    // Explicit block: U|c = I_s, V|c^1 = R|c^1 (L|c)^T.
+    DBuf<T> U2(c, (size_t)P * m * s), V2(c, (size_t)P * m * s);
+    set_identity_clusters<T>(c, P, m, s, U2.p, s, (long)m * s);
+    Op<T> A{Rb.p, r, 1, (long)m * r, (long)s * r, 0, 0, 1};
+    Op<T> B{Lb.p, 1, r, (long)m * r, (long)s * r, 0, 0, 0};
+    Op<T> C{V2.p, s, 1, (long)m * s, (long)s * s, 0, 0, 1};
+    gemm<T>(c, s, s, r, P, nclus, T(1), A, B, T(0), C);
+    Lb = std::move(U2);
+    Rb = std::move(V2);
+    r = s;
+  }
+  if (exact) {
+    Uout = std::move(Lb);
+    Vout = std::move(Rb);
+    Kout = r;
+    return;
+  }
+  const bool qr = (s <= 128);
+  DBuf<T> R(c, 2 * NB * r * (size_t)r);
+  DBuf<int> piv(c, 2 * NB * (size_t)r), kk(c, 2 * NB);
+  if (qr) {
+    size_t sm = ((size_t)s * r + r) * sizeof(T);
+    ACR_CUDA(cudaFuncSetAttribute(k_qr_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_qr_small<T><<<(unsigned)(2 * NB), 256, sm, c.st>>>(s, r, nclus, NB, (long)m * r, Lb.p, Rb.p, R.p, piv.p,
+                                                         kk.p);
+    c.launches++;
+  } else {
+    DBuf<T> G(c, 2 * NB * r * (size_t)r);
+    for (int side = 0; side < 2; ++side) {
+      T* F = side ? Rb.p : Lb.p;
+      Op<T> A{F, 1, r, (long)m * r, (long)s * r, 0, 0, side};
+      Op<T> B{F, r, 1, (long)m * r, (long)s * r, 0, 0, side};
+      Op<T> C{G.p + side * NB * r * (long)r, r, 1, (long)nclus * r * r, (long)r * r, 0, 0, 0};
+      gemm<T>(c, r, r, s, P, nclus, T(1), A, B, T(0), C);
+    }
+    double epsd = std::max(0.01 * tol * tol, sizeof(T) == 8 ? 1e-15 : 1e-5);
+    size_t sm = (size_t)r * sizeof(T);
+    if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_pchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_pchol<T><<<(unsigned)(2 * NB), 256, sm, c.st>>>(r, G.p, T(epsd), R.p, piv.p, kk.p);
+    c.launches++;
+  }
+  DBuf<T> Cc(c, NB * (size_t)r * r);
+  {
+    Op<T> A{R.p, r, 1, 0, (long)r * r, 0, 0, 0};
+    Op<T> B{R.p + NB * r * (long)r, 1, r, 0, (long)r * r, 0, 0, 0};
+    Op<T> C{Cc.p, r, 1, 0, (long)r * r, 0, 0, 0};
+    gemm<T>(c, r, r, r, 1, (int)NB, T(1), A, B, T(0), C);
+  }
+  DBuf<T> W(c, NB * (size_t)r * r), Vw(c, NB * (size_t)r * r), Xo(c, NB * (size_t)r * r),
+      Yo(c, NB * (size_t)r * r), sig(c, NB * (size_t)r);
+  DBuf<int> rank(c, NB);
+  {
+    size_t sm = (size_t)r * (sizeof(T) + sizeof(int));
+    if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_jacobi<T><<<(unsigned)NB, 256, sm, c.st>>>(r, Cc.p, kk.p, NB, W.p, Vw.p, Xo.p, Yo.p, sig.p, rank.p, T(tol),
+                                                 60);
+    c.launches++;
+  }
+  std::vector<int> hr(NB);
+  ACR_CUDA(cudaMemcpyAsync(hr.data(), rank.p, NB * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  ACR_CUDA(cudaStreamSynchronize(c.st));
+  Kout = 0;
+  for (int v : hr) Kout = std::max(Kout, v);
+  if (Kout == 0) {
+    Uout.release();
+    Vout.release();
+    return;
+  }
+  DBuf<T> Z(c, 2 * NB * (size_t)r * Kout);
+  k_coef<T><<<(unsigned)(2 * NB), 256, 0, c.st>>>(r, Kout, NB, qr ? 1 : 0, R.p, piv.p, kk.p, Xo.p, Yo.p, sig.p,
+                                                 rank.p, Z.p);
+  c.launches++;
+  Uout = DBuf<T>(c, (size_t)P * m * Kout);
+  Vout = DBuf<T>(c, (size_t)P * m * Kout);
+  for (int side = 0; side < 2; ++side) {
+    T* F = side ? Rb.p : Lb.p;
+    Op<T> A{F, r, 1, (long)m * r, (long)s * r, 0, 0, 0};
+    Op<T> B{Z.p + side * NB * r * (long)Kout, Kout, 1, (long)nclus * r * Kout, (long)r * Kout, 0, 0, side};
+    Op<T> C{(side ? Vout.p : Uout.p), Kout, 1, (long)m * Kout, (long)s * Kout, 0, 0, 0};
+    gemm<T>(c, s, Kout, r, P, nclus, T(1), A, B, T(0), C);
+  }
+}
+
+template void recompress_level<float>(Ctx&, int, int, int, DBuf<float>&&, DBuf<float>&&, int, double, bool,
+                                      DBuf<float>&, DBuf<float>&, int&);
+template void recompress_level<double>(Ctx&, int, int, int, DBuf<double>&&, DBuf<double>&&, int, double, bool,
+                                       DBuf<double>&, DBuf<double>&, int&);
+
+}  // namespace acr

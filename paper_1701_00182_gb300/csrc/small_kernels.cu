@@ -1,0 +1,565 @@
+// Element-wise and per-block kernels of the ACR path: fills and panel copies,
+// batched Gauss-Jordan inversion (leaves and Woodbury couplings), level-0
+// HODLR assembly of the 7-point planes, RHS permutations, and the FP64
+// 7-point stencil with its column reductions (residual, refinement, GMRES).
+#include <algorithm>
+#include <cmath>
+
+#include "acr_internal.h"
+
+namespace acr {
+
+namespace {
+inline int nblk(long tot, int bs = 256, int cap = 152 * 32) {
+  long b = (tot + bs - 1) / bs;
+  return (int)std::max(1L, std::min<long>(b, cap));
+}
+}  // namespace
+
+template <class T>
+__global__ void k_fill(T* p, long n, T v) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) p[i] = v;
+}
+template <class T>
+void fill(Ctx& c, T* p, long n, T v) {
+  if (n <= 0) return;
+  k_fill<T><<<nblk(n), 256, 0, c.st>>>(p, n, v);
+  c.launches++;
+}
+
+// dst[p][row][j] = alpha * src[p][row][j], j < cols.
+template <class T>
+__global__ void k_copy2d(int P, long rows, int cols, T alpha, const T* src, long sld, long sps, T* dst,
+                         long dld, long dps) {
+  long tot = (long)P * rows * cols;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    long p = e / (rows * cols);
+    long r = e - p * rows * cols;
+    long i = r / cols;
+    int j = (int)(r - i * cols);
+    dst[p * dps + i * dld + j] = alpha * src[p * sps + i * sld + j];
+  }
+}
+template <class T>
+void copy2d(Ctx& c, int P, long rows, int cols, T alpha, const T* src, long sld, long sps, T* dst, long dld,
+            long dps) {
+  long tot = (long)P * rows * cols;
+  if (tot <= 0) return;
+  if (c.check_bounds) {
+    c.check_range(src, 0, (long)(P - 1) * sps + (rows - 1) * sld + cols - 1, sizeof(T), "copy2d src");
+    c.check_range(dst, 0, (long)(P - 1) * dps + (rows - 1) * dld + cols - 1, sizeof(T), "copy2d dst");
+  }
+  k_copy2d<T><<<nblk(tot), 256, 0, c.st>>>(P, rows, cols, alpha, src, sld, sps, dst, dld, dps);
+  c.launches++;
+}
+
+// Every cluster (size s) of every plane: U|c = I_s  (panel of width s).
+template <class T>
+__global__ void k_identity(int P, int m, int s, T* U, long ld, long ps) {
+  long tot = (long)P * m * s;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    long p = e / ((long)m * s);
+    long r = e - p * (long)m * s;
+    long i = r / s;
+    int j = (int)(r - i * s);
+    U[p * ps + i * ld + j] = ((int)(i % s) == j) ? T(1) : T(0);
+  }
+}
+template <class T>
+void set_identity_clusters(Ctx& c, int P, int m, int s, T* U, long ld, long ps) {
+  long tot = (long)P * m * s;
+  if (tot <= 0) return;
+  k_identity<T><<<nblk(tot), 256, 0, c.st>>>(P, m, s, U, ld, ps);
+  c.launches++;
+}
+
+// In-place Gauss-Jordan inversion with partial (row) pivoting, one CTA per
+// matrix of order n (row major, matrices `stride` elements apart).  A pivot
+// below 64 u max|A| sets flag[0] = 1 and is replaced by that threshold so the
+// kernel always finishes.
+template <class T>
+__global__ void __launch_bounds__(256) k_gj_inverse(int n, T* A, long stride, int* flag) {
+  extern __shared__ unsigned char smraw[];
+  T* rowk = reinterpret_cast<T*>(smraw);
+  T* fcol = rowk + n;
+  int* piv = reinterpret_cast<int*>(fcol + n);
+  __shared__ T redv[256];
+  __shared__ int redi[256];
+  __shared__ T s_thr;
+  T* a = A + (long)blockIdx.x * stride;
+  const int tid = threadIdx.x;
+  // max |A| for the breakdown threshold
+  T mx = T(0);
+  for (long e = tid; e < (long)n * n; e += blockDim.x) mx = fmax(mx, fabs(a[e]));
+  redv[tid] = mx;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (tid < s) redv[tid] = fmax(redv[tid], redv[tid + s]);
+    __syncthreads();
+  }
+  const T eps = sizeof(T) == 8 ? T(1.1e-16) : T(6e-8);
+  if (tid == 0) s_thr = redv[0] > T(0) ? T(64) * eps * redv[0] : T(1e-30);
+  __syncthreads();
+  const T thr = s_thr;
+  for (int k = 0; k < n; ++k) {
+    T best = T(-1);
+    int bi = k;
+    for (int i = k + tid; i < n; i += blockDim.x) {
+      T v = fabs(a[(long)i * n + k]);
+      if (v > best) { best = v; bi = i; }
+    }
+    redv[tid] = best;
+    redi[tid] = bi;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (tid < s && (redv[tid + s] > redv[tid] || (redv[tid + s] == redv[tid] && redi[tid + s] < redi[tid]))) {
+        redv[tid] = redv[tid + s];
+        redi[tid] = redi[tid + s];
+      }
+      __syncthreads();
+    }
+    const int p = redi[0];
+    if (tid == 0) piv[k] = p;
+    if (p != k) {
+      for (int j = tid; j < n; j += blockDim.x) {
+        T t = a[(long)k * n + j];
+        a[(long)k * n + j] = a[(long)p * n + j];
+        a[(long)p * n + j] = t;
+      }
+    }
+    __syncthreads();
+    T d = a[(long)k * n + k];
+    if (!(fabs(d) > thr)) {
+      if (tid == 0 && flag) atomicExch(flag, 1);
+      d = (d < T(0)) ? -thr : thr;
+    }
+    const T inv = T(1) / d;
+    for (int j = tid; j < n; j += blockDim.x) rowk[j] = (j == k) ? inv : a[(long)k * n + j] * inv;
+    for (int i = tid; i < n; i += blockDim.x) fcol[i] = (i == k) ? T(0) : a[(long)i * n + k];
+    __syncthreads();
+    for (long e = tid; e < (long)n * n; e += blockDim.x) {
+      int i = (int)(e / n), j = (int)(e - (long)i * n);
+      if (i == k) {
+        a[e] = rowk[j];
+      } else {
+        T f = fcol[i];
+        if (f != T(0)) a[e] = ((j == k) ? T(0) : a[e]) - f * rowk[j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    int p = piv[k];
+    if (p != k) {
+      for (int i = tid; i < n; i += blockDim.x) {
+        T t = a[(long)i * n + k];
+        a[(long)i * n + k] = a[(long)i * n + p];
+        a[(long)i * n + p] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+int batched_inverse(Ctx& c, int nb, int n, T* A, long stride) {
+  if (nb <= 0 || n <= 0) return 0;
+  size_t sm = 2 * (size_t)n * sizeof(T) + (size_t)n * sizeof(int);
+  if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_gj_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  if (sm > 200 * 1024) throw AcrError(4, "coupling matrix too large");
+  k_gj_inverse<T><<<nb, 256, sm, c.st>>>(n, A, stride, c.d_flag);
+  c.launches++;
+  return 0;
+}
+
+// Woodbury coupling of node t at one level, rows swapped so that its inverse
+// is directly the operator applied to the stacked child coefficients:
+//   M'_t = [[g(2t), I], [I, g(2t+1)]],  g(c) = V|c^T (X U)|c  (K x K).
+template <class T>
+__global__ void k_build_coupling(int P, int nodes, int K, const T* g, T* M) {
+  long K2 = 2L * K;
+  long tot = (long)P * nodes * K2 * K2;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    long nt = e / (K2 * K2);
+    long r = e - nt * K2 * K2;
+    int i = (int)(r / K2), j = (int)(r % K2);
+    int a = i >= K, b = j >= K;
+    int ii = i - a * K, jj = j - b * K;
+    T v;
+    if (a == b) v = g[((nt * 2 + a) * K + ii) * (long)K + jj];
+    else v = (ii == jj) ? T(1) : T(0);
+    M[e] = v;
+  }
+}
+template <class T>
+void build_coupling(Ctx& c, int P, int nodes, int K, const T* g, T* Mout) {
+  long tot = (long)P * nodes * 4L * K * K;
+  if (tot <= 0) return;
+  k_build_coupling<T><<<nblk(tot), 256, 0, c.st>>>(P, nodes, K, g, Mout);
+  c.launches++;
+}
+
+// ---- level-0 assembly --------------------------------------------------------
+
+__device__ __forceinline__ double harm(double a, double b, double ih2) { return 2.0 * a * b / (a + b) * ih2; }
+
+// One thread per row of a leaf block of plane k: the 5-point in-plane part
+// restricted to the leaf, the full diagonal (6 faces + shift), and the
+// diagonal E (to plane k-1) and F (to plane k+1) entries.
+template <class T>
+__global__ void k_assemble_leaves(int n, int b, const double* kap, double shift, const int* perm,
+                                  const int* iperm, T* DL, T* EL, T* FL) {
+  const int m = n * n;
+  const int nleaf = m / b;
+  const int k = blockIdx.x / nleaf, lf = blockIdx.x % nleaf;
+  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+  for (int i = threadIdx.x; i < b; i += blockDim.x) {
+    const int pos = lf * b + i;
+    const int g = perm[pos];
+    const int x = g % n, y = g / n;
+    const long node = (long)k * m + g;
+    const double kp = kap[node];
+    T* drow = DL + ((long)k * nleaf + lf) * b * b + (long)i * b;
+    T* erow = EL + ((long)k * nleaf + lf) * b * b + (long)i * b;
+    T* frow = FL + ((long)k * nleaf + lf) * b * b + (long)i * b;
+    for (int j = 0; j < b; ++j) { drow[j] = T(0); erow[j] = T(0); frow[j] = T(0); }
+    double diag = shift;
+    const int dx[4] = {-1, 1, 0, 0}, dy[4] = {0, 0, -1, 1};
+    for (int d = 0; d < 4; ++d) {
+      int xx = x + dx[d], yy = y + dy[d];
+      if (xx < 0 || xx >= n || yy < 0 || yy >= n) { diag += kp * ih2; continue; }
+      double cpq = harm(kp, kap[(long)k * m + xx + n * yy], ih2);
+      diag += cpq;
+      int q = iperm[xx + n * yy];
+      if (q >= lf * b && q < lf * b + b) drow[q - lf * b] = T(-cpq);
+    }
+    if (k > 0) { double cz = harm(kp, kap[node - m], ih2); diag += cz; erow[i] = T(-cz); }
+    else diag += kp * ih2;
+    if (k < n - 1) { double cz = harm(kp, kap[node + m], ih2); diag += cz; frow[i] = T(-cz); }
+    else diag += kp * ih2;
+    drow[i] = T(diag);
+  }
+}
+
+// One thread per (plane, cut edge) of a level: the exact low-rank factors of
+// the off-diagonal blocks, one column per cut edge (p in the first child,
+// q in the second):  U[p,e] = U[q,e] = -c_pq,  V[p,e] = V[q,e] = 1.
+template <class T>
+__global__ void k_assemble_cuts(int n, int nodes, int ncut, const double* kap, const int* perm,
+                                const int* cp, const int* cq, T* U, T* V, long ld, long ps) {
+  const int m = n * n;
+  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+  long tot = (long)n * nodes * ncut;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    int k = (int)(e / ((long)nodes * ncut));
+    int r = (int)(e - (long)k * nodes * ncut);
+    int col = r % ncut;
+    int p = cp[r], q = cq[r];
+    double c = harm(kap[(long)k * m + perm[p]], kap[(long)k * m + perm[q]], ih2);
+    U[k * ps + (long)p * ld + col] = T(-c);
+    U[k * ps + (long)q * ld + col] = T(-c);
+    V[k * ps + (long)p * ld + col] = T(1);
+    V[k * ps + (long)q * ld + col] = T(1);
+  }
+}
+
+template <class T>
+void assemble_level0(Ctx& c, const Geometry& geo, const double* kappa, double shift, const int* d_perm,
+                     const int* d_iperm, const std::vector<const int*>& d_cutp,
+                     const std::vector<const int*>& d_cutq, HMat<T> D, HMat<T> E, HMat<T> F) {
+  const int n = geo.n, b = geo.leaf;
+  const int nleaf = geo.m / b;
+  k_assemble_leaves<T><<<n * nleaf, std::min(b, 128), 0, c.st>>>(n, b, kappa, shift, d_perm, d_iperm, D.leaf,
+                                                                 E.leaf, F.leaf);
+  c.launches++;
+  for (int l = 0; l < geo.L; ++l) {
+    int K = geo.ncut[l];
+    fill<T>(c, D.U[l], (long)n * D.pps[l], T(0));
+    fill<T>(c, D.V[l], (long)n * D.pps[l], T(0));
+    long tot = (long)n * (1L << l) * K;
+    k_assemble_cuts<T><<<nblk(tot), 256, 0, c.st>>>(n, 1 << l, K, kappa, d_perm, d_cutp[l], d_cutq[l], D.U[l],
+                                                   D.V[l], K, D.pps[l]);
+    c.launches++;
+  }
+}
+
+// ---- RHS permutations --------------------------------------------------------
+// F[k][pos][c] (row major per plane, nrhs contiguous) <-> x[perm[pos] + m k + c ld].
+
+template <class T>
+__global__ void k_permute_in(int n, int nrhs, const double* b, long ld, const int* perm, T* F) {
+  __shared__ double tile[32][33];
+  const int m = n * n;
+  const long rowblk = blockIdx.x;  // over (k, pos/32)
+  const int k = (int)(rowblk / ((m + 31) / 32));
+  const int p0 = (int)(rowblk % ((m + 31) / 32)) * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int yy = ty; yy < 32; yy += 8) {
+    int c = c0 + yy, pos = p0 + tx;
+    tile[yy][tx] = (c < nrhs && pos < m) ? b[(long)perm[pos] + (long)m * k + (long)c * ld] : 0.0;
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    int pos = p0 + yy, c = c0 + tx;
+    if (pos < m && c < nrhs) F[((long)k * m + pos) * nrhs + c] = T(tile[tx][yy]);
+  }
+}
+template <class T>
+void permute_in(Ctx& c, int n, int nrhs, const double* b, long ld, const int* d_perm, T* F) {
+  int m = n * n;
+  dim3 grid((unsigned)((long)n * ((m + 31) / 32)), (nrhs + 31) / 32);
+  k_permute_in<T><<<grid, dim3(32, 8), 0, c.st>>>(n, nrhs, b, ld, d_perm, F);
+  c.launches++;
+}
+
+template <class T>
+__global__ void k_permute_out(int n, int nrhs, const T* F, const int* perm, double* x, long ld, int acc) {
+  __shared__ double tile[32][33];
+  const int m = n * n;
+  const long rowblk = blockIdx.x;
+  const int k = (int)(rowblk / ((m + 31) / 32));
+  const int p0 = (int)(rowblk % ((m + 31) / 32)) * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int yy = ty; yy < 32; yy += 8) {
+    int pos = p0 + yy, c = c0 + tx;
+    tile[yy][tx] = (pos < m && c < nrhs) ? (double)F[((long)k * m + pos) * nrhs + c] : 0.0;
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    int c = c0 + yy, pos = p0 + tx;
+    if (c < nrhs && pos < m) {
+      double* dst = x + (long)perm[pos] + (long)m * k + (long)c * ld;
+      *dst = acc ? *dst + tile[tx][yy] : tile[tx][yy];
+    }
+  }
+}
+template <class T>
+void permute_out(Ctx& c, int n, int nrhs, const T* F, const int* d_perm, double* x, long ld, int accumulate) {
+  int m = n * n;
+  dim3 grid((unsigned)((long)n * ((m + 31) / 32)), (nrhs + 31) / 32);
+  k_permute_out<T><<<grid, dim3(32, 8), 0, c.st>>>(n, nrhs, F, d_perm, x, ld, accumulate);
+  c.launches++;
+}
+
+// ---- FP64 7-point stencil ------------------------------------------------------
+// coef layout: [4][N] = diagonal (6 faces + shift), coupling to +x, +y, +z.
+
+__global__ void k_face_coef(int n, const double* kap, double shift, double* coef) {
+  const long N = (long)n * n * n;
+  const int m = n * n;
+  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x) {
+    int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / m);
+    double kp = kap[p];
+    double d = shift;
+    double cx = 0, cy = 0, cz = 0;
+    d += (x > 0) ? harm(kp, kap[p - 1], ih2) : kp * ih2;
+    if (x < n - 1) { cx = harm(kp, kap[p + 1], ih2); d += cx; } else d += kp * ih2;
+    d += (y > 0) ? harm(kp, kap[p - n], ih2) : kp * ih2;
+    if (y < n - 1) { cy = harm(kp, kap[p + n], ih2); d += cy; } else d += kp * ih2;
+    d += (z > 0) ? harm(kp, kap[p - m], ih2) : kp * ih2;
+    if (z < n - 1) { cz = harm(kp, kap[p + m], ih2); d += cz; } else d += kp * ih2;
+    coef[p] = d;
+    coef[N + p] = cx;
+    coef[2 * N + p] = cy;
+    coef[3 * N + p] = cz;
+  }
+}
+void face_coefficients(Ctx& c, int n, const double* kappa, double shift, double* coef) {
+  long N = (long)n * n * n;
+  k_face_coef<<<nblk(N), 256, 0, c.st>>>(n, kappa, shift, coef);
+  c.launches++;
+}
+
+// out = alpha * A x + beta * y; optional per-column partial sums of out^2 and y^2.
+__global__ void k_stencil(int n, int nrhs, const double* __restrict__ coef, const double* __restrict__ x, long ld,
+                          const double* y, double* out, double alpha, double beta, double* part) {
+  const long N = (long)n * n * n;
+  const int m = n * n;
+  const int col = blockIdx.y;
+  __shared__ double s1[256], s2[256];
+  double a1 = 0, a2 = 0;
+  const double* xc = x + (long)col * ld;
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x) {
+    int xi = (int)(p % n), yi = (int)((p / n) % n), zi = (int)(p / m);
+    double v = coef[p] * xc[p];
+    if (xi < n - 1) v -= coef[N + p] * xc[p + 1];
+    if (xi > 0) v -= coef[N + p - 1] * xc[p - 1];
+    if (yi < n - 1) v -= coef[2 * N + p] * xc[p + n];
+    if (yi > 0) v -= coef[2 * N + p - n] * xc[p - n];
+    if (zi < n - 1) v -= coef[3 * N + p] * xc[p + m];
+    if (zi > 0) v -= coef[3 * N + p - m] * xc[p - m];
+    double yv = (beta != 0.0) ? y[(long)col * ld + p] : 0.0;
+    double o = alpha * v + beta * yv;
+    out[(long)col * ld + p] = o;
+    a1 += o * o;
+    a2 += yv * yv;
+  }
+  if (!part) return;
+  s1[threadIdx.x] = a1;
+  s2[threadIdx.x] = a2;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) { s1[threadIdx.x] += s1[threadIdx.x + s]; s2[threadIdx.x] += s2[threadIdx.x + s]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[((long)col * gridDim.x + blockIdx.x) * 2] = s1[0];
+    part[((long)col * gridDim.x + blockIdx.x) * 2 + 1] = s2[0];
+  }
+}
+
+__global__ void k_reduce_pairs(int nrhs, int nparts, const double* part, double* out) {
+  int col = blockIdx.x;
+  __shared__ double s1[256], s2[256];
+  double a1 = 0, a2 = 0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    a1 += part[((long)col * nparts + i) * 2];
+    a2 += part[((long)col * nparts + i) * 2 + 1];
+  }
+  s1[threadIdx.x] = a1;
+  s2[threadIdx.x] = a2;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) { s1[threadIdx.x] += s1[threadIdx.x + s]; s2[threadIdx.x] += s2[threadIdx.x + s]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[2 * col] = s1[0]; out[2 * col + 1] = s2[0]; }
+}
+
+void stencil_apply(Ctx& c, int n, int nrhs, const double* coef, const double* x, long ld, const double* y,
+                   double* out, double alpha, double beta, double* norms_out) {
+  long N = (long)n * n * n;
+  int nb = (int)std::min<long>((N + 255) / 256, 1024);
+  double* part = nullptr;
+  if (norms_out) part = c.alloc<double>((size_t)nb * nrhs * 2);
+  k_stencil<<<dim3(nb, nrhs), 256, 0, c.st>>>(n, nrhs, coef, x, ld, y, out, alpha, beta, part);
+  c.launches++;
+  if (norms_out) {
+    k_reduce_pairs<<<nrhs, 256, 0, c.st>>>(nrhs, nb, part, norms_out);
+    c.launches++;
+    c.free(part, (size_t)nb * nrhs * 2);
+  }
+}
+
+__global__ void k_col_dots(long N, const double* x, long ldx, const double* y, long ldy, double* part) {
+  int col = blockIdx.y;
+  __shared__ double s1[256];
+  double a = 0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+    a += x[(long)col * ldx + i] * y[(long)col * ldy + i];
+  s1[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) s1[threadIdx.x] += s1[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[((long)col * gridDim.x + blockIdx.x) * 2] = s1[0];
+    part[((long)col * gridDim.x + blockIdx.x) * 2 + 1] = 0.0;
+  }
+}
+void col_dots(Ctx& c, long N, int nrhs, const double* x, long ldx, const double* y, long ldy, double* out) {
+  int nb = (int)std::min<long>((N + 255) / 256, 512);
+  double* part = c.alloc<double>((size_t)nb * nrhs * 2);
+  double* pairs = c.alloc<double>((size_t)nrhs * 2);
+  k_col_dots<<<dim3(nb, nrhs), 256, 0, c.st>>>(N, x, ldx, y, ldy, part);
+  k_reduce_pairs<<<nrhs, 256, 0, c.st>>>(nrhs, nb, part, pairs);
+  k_copy2d<double><<<1, 64, 0, c.st>>>(1, nrhs, 1, 1.0, pairs, 2, 0, out, 1, 0);
+  c.launches += 3;
+  c.free(part, (size_t)nb * nrhs * 2);
+  c.free(pairs, (size_t)nrhs * 2);
+}
+
+__global__ void k_col_axpy(long N, int nrhs, const double* a, const double* x, long ldx, double* y, long ldy,
+                           int overwrite) {
+  long tot = N * nrhs;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    int col = (int)(e / N);
+    long i = e - (long)col * N;
+    double v = a[col] * x[(long)col * ldx + i];
+    if (overwrite) y[(long)col * ldy + i] = v;
+    else y[(long)col * ldy + i] += v;
+  }
+}
+void col_axpy(Ctx& c, long N, int nrhs, const double* a, const double* x, long ldx, double* y, long ldy) {
+  k_col_axpy<<<nblk(N * nrhs), 256, 0, c.st>>>(N, nrhs, a, x, ldx, y, ldy, 0);
+  c.launches++;
+}
+void col_scale_copy(Ctx& c, long N, int nrhs, const double* a, const double* x, long ldx, double* y, long ldy) {
+  k_col_axpy<<<nblk(N * nrhs), 256, 0, c.st>>>(N, nrhs, a, x, ldx, y, ldy, 1);
+  c.launches++;
+}
+
+
+// dst[p][row][j] += alpha * src[p][row][j], j < cols.
+template <class T>
+__global__ void k_axpy2d(int P, long rows, int cols, T alpha, const T* src, long sld, long sps, T* dst, long dld,
+                         long dps) {
+  long tot = (long)P * rows * cols;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    long p = e / (rows * cols);
+    long r = e - p * rows * cols;
+    long i = r / cols;
+    int j = (int)(r - i * cols);
+    dst[p * dps + i * dld + j] += alpha * src[p * sps + i * sld + j];
+  }
+}
+template <class T>
+void axpy2d(Ctx& c, int P, long rows, int cols, T alpha, const T* src, long sld, long sps, T* dst, long dld,
+            long dps) {
+  long tot = (long)P * rows * cols;
+  if (tot <= 0) return;
+  if (c.check_bounds) {
+    c.check_range(src, 0, (long)(P - 1) * sps + (rows - 1) * sld + cols - 1, sizeof(T), "axpy2d src");
+    c.check_range(dst, 0, (long)(P - 1) * dps + (rows - 1) * dld + cols - 1, sizeof(T), "axpy2d dst");
+  }
+  k_axpy2d<T><<<nblk(tot), 256, 0, c.st>>>(P, rows, cols, alpha, src, sld, sps, dst, dld, dps);
+  c.launches++;
+}
+
+// Dense m x m image of the leaf blocks of one HODLR matrix (off-diagonal zero).
+template <class T>
+__global__ void k_expand_leaves(int m, int b, const T* leaf, T* dense) {
+  long tot = (long)m * b;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    long row = e / b;
+    int j = (int)(e % b);
+    long lf = row / b;
+    dense[row * m + lf * b + j] = leaf[e];
+  }
+}
+template <class T>
+void expand_leaves(Ctx& c, int m, int b, const T* leaf, T* dense) {
+  k_expand_leaves<T><<<nblk((long)m * b), 256, 0, c.st>>>(m, b, leaf, dense);
+  c.launches++;
+}
+
+__global__ void k_exp_inplace(double* p, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) p[i] = exp(p[i]);
+}
+void exp_inplace(Ctx& c, double* p, long n) {
+  k_exp_inplace<<<nblk(n), 256, 0, c.st>>>(p, n);
+  c.launches++;
+}
+
+#define INST(T)                                                                                          \
+  template void fill<T>(Ctx&, T*, long, T);                                                              \
+  template void copy2d<T>(Ctx&, int, long, int, T, const T*, long, long, T*, long, long);                \
+  template void set_identity_clusters<T>(Ctx&, int, int, int, T*, long, long);                           \
+  template int batched_inverse<T>(Ctx&, int, int, T*, long);                                             \
+  template void build_coupling<T>(Ctx&, int, int, int, const T*, T*);                                    \
+  template void assemble_level0<T>(Ctx&, const Geometry&, const double*, double, const int*, const int*, \
+                                   const std::vector<const int*>&, const std::vector<const int*>&,       \
+                                   HMat<T>, HMat<T>, HMat<T>);                                           \
+  template void permute_in<T>(Ctx&, int, int, const double*, long, const int*, T*);                      \
+  template void permute_out<T>(Ctx&, int, int, const T*, const int*, double*, long, int);                \
+  template void axpy2d<T>(Ctx&, int, long, int, T, const T*, long, long, T*, long, long);                \
+  template void expand_leaves<T>(Ctx&, int, int, const T*, T*);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace acr

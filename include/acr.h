@@ -63,6 +63,7 @@ typedef struct {
   int autotune;           /* 1 = time candidate GEMM tilings per shape class and keep the fastest */
   int nrhs_max;           /* solve workspace is sized for this many right-hand sides (default 64) */
   void* cuda_stream;      /* cudaStream_t to run on; NULL = legacy default stream */
+  int profile;            /* 1 = time every kernel launch with CUDA events (per-class totals in acr_stats) */
 } acr_opts;
 
 typedef struct {
@@ -77,6 +78,14 @@ typedef struct {
   double t_level_ms[16];                  /* per CR level */
   long long gemm_flops;                   /* algorithmic GEMM flops issued by the factorisation */
   long long kernel_launches;              /* kernels launched by the last call */
+  /* Per kernel class, accumulated over the handle's life (times only with opts.profile = 1):
+   * 0 batched GEMM, 1 split-K reduction, 2 Householder QR, 3 pivoted Cholesky, 4 Jacobi SVD,
+   * 5 rebuild coefficients, 6 Gauss-Jordan inverse, 7 copies/fills, 8 assembly, 9 RHS permutation,
+   * 10 FP64 stencil and column reductions.  flops/bytes are algorithmic counts (each operand once). */
+  double kc_ms[16];
+  double kc_flops[16];
+  double kc_bytes[16];
+  long long kc_launches[16];
 } acr_stats;
 
 /* Default options (FP64, shift 0, unlimited ranks and memory, autotune off, nrhs_max 64). */

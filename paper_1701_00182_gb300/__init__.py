@@ -30,6 +30,8 @@ ACR_ERR_CUDA = 5
 ACR_ERR_NOT_CONVERGED = 6
 ACR_FP64 = 0
 ACR_FP32 = 1
+KERNEL_CLASSES = ("gemm", "splitk_reduce", "householder_qr", "pivoted_cholesky", "jacobi_svd", "rebuild_coef",
+                  "gauss_jordan", "copy", "assemble", "permute", "stencil_fp64")
 
 
 class AcrOpts(C.Structure):
@@ -41,6 +43,7 @@ class AcrOpts(C.Structure):
         ("autotune", C.c_int),
         ("nrhs_max", C.c_int),
         ("cuda_stream", C.c_void_p),
+        ("profile", C.c_int),
     ]
 
 
@@ -60,6 +63,10 @@ class AcrStats(C.Structure):
         ("t_level_ms", C.c_double * 16),
         ("gemm_flops", C.c_longlong),
         ("kernel_launches", C.c_longlong),
+        ("kc_ms", C.c_double * 16),
+        ("kc_flops", C.c_double * 16),
+        ("kc_bytes", C.c_double * 16),
+        ("kc_launches", C.c_longlong * 16),
     ]
 
 
@@ -271,6 +278,8 @@ def acr_get_stats(h: Handle) -> dict:
         "factor_bytes": s.factor_bytes, "peak_bytes": s.peak_bytes, "t_factor_ms": s.t_factor_ms,
         "t_level_ms": [s.t_level_ms[r] for r in range(min(q, 16))], "gemm_flops": s.gemm_flops,
         "kernel_launches": s.kernel_launches,
+        "kernels": {nm: {"ms": s.kc_ms[i], "flops": s.kc_flops[i], "bytes": s.kc_bytes[i],
+                         "launches": s.kc_launches[i]} for i, nm in enumerate(KERNEL_CLASSES)},
     }
 
 

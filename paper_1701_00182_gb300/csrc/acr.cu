@@ -42,6 +42,49 @@ void* Ctx::dalloc_bytes(size_t bytes) {
   return p;
 }
 
+void Ctx::kbegin() {
+  if (!profile) return;
+  if (evfree.empty()) {
+    cudaEvent_t e;
+    ACR_CUDA(cudaEventCreate(&e));
+    evfree.push_back(e);
+  }
+  evcur = evfree.back();
+  evfree.pop_back();
+  ACR_CUDA(cudaEventRecord(evcur, st));
+}
+
+void Ctx::kend(int cls, double flops, double bytes) {
+  ++launches;
+  kc_launch[cls] += 1;
+  kc_flops[cls] += flops;
+  kc_bytes[cls] += bytes;
+  if (!profile || !evcur) return;
+  if (evfree.empty()) {
+    cudaEvent_t e;
+    ACR_CUDA(cudaEventCreate(&e));
+    evfree.push_back(e);
+  }
+  cudaEvent_t b = evfree.back();
+  evfree.pop_back();
+  ACR_CUDA(cudaEventRecord(b, st));
+  pend.push_back({evcur, b, cls});
+  evcur = nullptr;
+  if (pend.size() >= 8192) kflush();
+}
+
+void Ctx::kflush() {
+  if (pend.empty()) return;
+  ACR_CUDA(cudaStreamSynchronize(st));
+  for (auto& p : pend) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) kc_ms[p.cls] += ms;
+    evfree.push_back(p.a);
+    evfree.push_back(p.b);
+  }
+  pend.clear();
+}
+
 void Ctx::check_range(const void* base, long lo, long hi, size_t es, const char* what) const {
   uintptr_t a = (uintptr_t)base + (intptr_t)lo * (intptr_t)es;
   uintptr_t b = (uintptr_t)base + (intptr_t)(hi + 1) * (intptr_t)es;
@@ -114,6 +157,9 @@ struct acr_handle_s {
     kappa.release();
     coef.release();
     if (ctx.d_flag) cudaFree(ctx.d_flag);
+    if (ctx.st) cudaStreamSynchronize(ctx.st);
+    for (auto& p : ctx.pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : ctx.evfree) cudaEventDestroy(e);
     if (ctx.st) cudaStreamSynchronize(ctx.st);
   }
 };
@@ -325,6 +371,16 @@ void solve_impl(acr_handle_s* h, FactorT<T>& fac, const double* rhs, double* x, 
   permute_out<T>(c, n, nrhs, Fint, h->perm.p, x, ld, accumulate ? 1 : 0);
 }
 
+void publish_profile(acr_handle_s* h) {
+  h->ctx.kflush();
+  for (int k = 0; k < KC_N; ++k) {
+    h->stats.kc_ms[k] = h->ctx.kc_ms[k];
+    h->stats.kc_flops[k] = h->ctx.kc_flops[k];
+    h->stats.kc_bytes[k] = h->ctx.kc_bytes[k];
+    h->stats.kc_launches[k] = h->ctx.kc_launch[k];
+  }
+}
+
 void solve_any(acr_handle_s* h, const double* rhs, double* x, int nrhs, long ld, bool trans, bool acc) {
   if (h->f64) solve_impl<double>(h, *h->f64, rhs, x, nrhs, ld, trans, acc);
   else solve_impl<float>(h, *h->f32, rhs, x, nrhs, ld, trans, acc);
@@ -430,6 +486,7 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     const char* cb = std::getenv("ACR_CHECK_BOUNDS");
     c.check_bounds = cb && cb[0] == '1';
     c.autotune = o.autotune != 0;
+    c.profile = o.profile != 0;
     ACR_CUDA(cudaMalloc(&c.d_flag, sizeof(int)));
     ACR_CUDA(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.st));
     h->n = n;
@@ -500,6 +557,7 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     h->stats.peak_bytes = c.peak_bytes;
     h->stats.gemm_flops = c.gemm_flops;
     h->stats.kernel_launches = c.launches;
+    publish_profile(h.get());
     if (h->max_rank > 0)
       for (int r = 0; r < 16; ++r)
         for (int l = 0; l < 16; ++l)
@@ -518,6 +576,7 @@ int acr_solve(acr_handle h, const double* rhs, double* x, int nrhs, long ld) {
     solve_any(h, rhs, x, nrhs, ld, false, false);
     h->stats.kernel_launches = h->ctx.launches;
     ACR_CUDA(cudaStreamSynchronize(h->ctx.st));
+    publish_profile(h);
   });
 }
 
@@ -528,6 +587,7 @@ int acr_solve_transpose(acr_handle h, const double* rhs, double* x, int nrhs, lo
     solve_any(h, rhs, x, nrhs, ld, true, false);
     h->stats.kernel_launches = h->ctx.launches;
     ACR_CUDA(cudaStreamSynchronize(h->ctx.st));
+    publish_profile(h);
   });
 }
 
@@ -575,6 +635,7 @@ int acr_solve_ir(acr_handle h, const double* b, double* x, int nrhs, long ld, do
     if (it > maxit) it = maxit;
     if (rel_res) std::memcpy(rel_res, rel.data(), nrhs * sizeof(double));
     h->stats.kernel_launches = h->ctx.launches;
+    publish_profile(h);
   });
   if (iters) *iters = it;
   if (st != ACR_OK) return st;
@@ -703,6 +764,7 @@ int acr_solve_fgmres(acr_handle h, const double* b, double* x, int nrhs, long ld
     }
     if (rel_res) std::memcpy(rel_res, rel.data(), nrhs * sizeof(double));
     h->stats.kernel_launches = h->ctx.launches;
+    publish_profile(h);
   });
   if (iters) *iters = total;
   if (st != ACR_OK) return st;

@@ -38,6 +38,10 @@ struct AcrError : std::runtime_error {
     }                                                                                    \
   } while (0)
 
+// Kernel classes for the per-class profile (CUDA events on the launch stream).
+enum KClass { KC_GEMM, KC_SPLITK, KC_QR, KC_PCHOL, KC_JACOBI, KC_COEF, KC_GJ, KC_COPY, KC_ASSEMBLE, KC_PERMUTE,
+              KC_STENCIL, KC_N };
+
 // Execution context of one handle: stream, scratch, counters, autotune cache.
 struct Ctx {
   cudaStream_t st = nullptr;
@@ -50,6 +54,16 @@ struct Ctx {
   std::map<uintptr_t, size_t> live;  // allocation start -> bytes (for the operand extent check)
   bool check_bounds = false;         // ACR_CHECK_BOUNDS=1: verify every GEMM operand range on the host
   void check_range(const void* base, long lo, long hi, size_t es, const char* what) const;
+  bool profile = false;  // record CUDA events around every launch, accumulated per kernel class
+  double kc_ms[16] = {}, kc_flops[16] = {}, kc_bytes[16] = {};
+  long long kc_launch[16] = {};
+  struct PendingEv { cudaEvent_t a, b; int cls; };
+  std::vector<cudaEvent_t> evfree;
+  std::vector<PendingEv> pend;
+  cudaEvent_t evcur = nullptr;
+  void kbegin();
+  void kend(int cls, double flops, double bytes);
+  void kflush();
   void* dalloc_bytes(size_t bytes);
   void dfree(void* p, size_t bytes);
   template <class T> T* alloc(size_t n) { return static_cast<T*>(dalloc_bytes(n * sizeof(T))); }

@@ -209,17 +209,23 @@ static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch
     T* part = c.alloc<T>(pn);
     g.kchunk = kchunk;
     g.partial = part;
+    const double es = sizeof(T);
+    c.kbegin();
     launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, split), g, c.st);
+    c.kend(KC_GEMM, 2.0 * M * N * K * batch, es * batch * ((double)M * K + (double)K * N + (double)M * N * split));
     long tot = batch * (long)M * N;
     int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
+    c.kbegin();
     k_splitk_reduce<T><<<nb, 256, 0, c.st>>>(g, split);
-    c.launches += 2;
+    c.kend(KC_SPLITK, (double)tot * split, es * tot * (split + 1 + (g.beta != T(0))));
     c.free(part, pn);
   } else {
     g.kchunk = K;
     g.partial = nullptr;
+    c.kbegin();
     launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, 1), g, c.st);
-    c.launches += 1;
+    c.kend(KC_GEMM, 2.0 * M * N * K * batch,
+           (double)sizeof(T) * batch * ((double)M * K + (double)K * N + (double)M * N * (1 + (g.beta != T(0)))));
   }
 }
 
@@ -260,8 +266,9 @@ void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A,
     GArgs<T> g{M, N, 0, nclus, (int)batch, T(0), beta, A, B, C, 0, nullptr};
     long tot = batch * (long)M * N;
     int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
+    c.kbegin();
     k_scale_c<T><<<nb, 256, 0, c.st>>>(g);
-    c.launches += 1;
+    c.kend(KC_COPY, 0, 2.0 * sizeof(T) * tot);
     return;
   }
   if (batch > 0x7fffffffL) throw AcrError(1, "gemm batch too large");

@@ -385,9 +385,10 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
   if (qr) {
     size_t sm = ((size_t)s * r + r) * sizeof(T);
     ACR_CUDA(cudaFuncSetAttribute(k_qr_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    c.kbegin();
     k_qr_small<T><<<(unsigned)(2 * NB), 256, sm, c.st>>>(s, r, nclus, NB, (long)m * r, Lb.p, Rb.p, R.p, piv.p,
                                                          kk.p);
-    c.launches++;
+    c.kend(KC_QR, 2.0 * NB * 4.0 * s * (double)r * r, 2.0 * NB * sizeof(T) * (2.0 * s * r + (double)r * r));
   } else {
     DBuf<T> G(c, 2 * NB * r * (size_t)r);
     for (int side = 0; side < 2; ++side) {
@@ -400,8 +401,9 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     double epsd = std::max(0.01 * tol * tol, sizeof(T) == 8 ? 1e-15 : 1e-5);
     size_t sm = (size_t)r * sizeof(T);
     if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_pchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    c.kbegin();
     k_pchol<T><<<(unsigned)(2 * NB), 256, sm, c.st>>>(r, G.p, T(epsd), R.p, piv.p, kk.p);
-    c.launches++;
+    c.kend(KC_PCHOL, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r);
   }
   DBuf<T> Cc(c, NB * (size_t)r * r);
   {
@@ -416,9 +418,10 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
   {
     size_t sm = (size_t)r * (sizeof(T) + sizeof(int));
     if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    c.kbegin();
     k_jacobi<T><<<(unsigned)NB, 256, sm, c.st>>>(r, Cc.p, kk.p, NB, W.p, Vw.p, Xo.p, Yo.p, sig.p, rank.p, T(tol),
                                                  60);
-    c.launches++;
+    c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r);
   }
   std::vector<int> hr(NB);
   ACR_CUDA(cudaMemcpyAsync(hr.data(), rank.p, NB * sizeof(int), cudaMemcpyDeviceToHost, c.st));
@@ -431,9 +434,10 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     return;
   }
   DBuf<T> Z(c, 2 * NB * (size_t)r * Kout);
+  c.kbegin();
   k_coef<T><<<(unsigned)(2 * NB), 256, 0, c.st>>>(r, Kout, NB, qr ? 1 : 0, R.p, piv.p, kk.p, Xo.p, Yo.p, sig.p,
                                                  rank.p, Z.p);
-  c.launches++;
+  c.kend(KC_COEF, 0, 2.0 * NB * sizeof(T) * ((double)r * r + (double)r * Kout));
   Uout = DBuf<T>(c, (size_t)P * m * Kout);
   Vout = DBuf<T>(c, (size_t)P * m * Kout);
   for (int side = 0; side < 2; ++side) {

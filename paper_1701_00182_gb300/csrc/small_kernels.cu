@@ -23,8 +23,9 @@ __global__ void k_fill(T* p, long n, T v) {
 template <class T>
 void fill(Ctx& c, T* p, long n, T v) {
   if (n <= 0) return;
+  c.kbegin();
   k_fill<T><<<nblk(n), 256, 0, c.st>>>(p, n, v);
-  c.launches++;
+  c.kend(KC_COPY, 0, (double)sizeof(T) * n);
 }
 
 // dst[p][row][j] = alpha * src[p][row][j], j < cols.
@@ -49,8 +50,9 @@ void copy2d(Ctx& c, int P, long rows, int cols, T alpha, const T* src, long sld,
     c.check_range(src, 0, (long)(P - 1) * sps + (rows - 1) * sld + cols - 1, sizeof(T), "copy2d src");
     c.check_range(dst, 0, (long)(P - 1) * dps + (rows - 1) * dld + cols - 1, sizeof(T), "copy2d dst");
   }
+  c.kbegin();
   k_copy2d<T><<<nblk(tot), 256, 0, c.st>>>(P, rows, cols, alpha, src, sld, sps, dst, dld, dps);
-  c.launches++;
+  c.kend(KC_COPY, 0, 2.0 * sizeof(T) * tot);
 }
 
 // Every cluster (size s) of every plane: U|c = I_s  (panel of width s).
@@ -69,8 +71,9 @@ template <class T>
 void set_identity_clusters(Ctx& c, int P, int m, int s, T* U, long ld, long ps) {
   long tot = (long)P * m * s;
   if (tot <= 0) return;
+  c.kbegin();
   k_identity<T><<<nblk(tot), 256, 0, c.st>>>(P, m, s, U, ld, ps);
-  c.launches++;
+  c.kend(KC_COPY, 0, (double)sizeof(T) * tot);
 }
 
 // In-place Gauss-Jordan inversion with partial (row) pivoting, one CTA per
@@ -167,8 +170,9 @@ int batched_inverse(Ctx& c, int nb, int n, T* A, long stride) {
   size_t sm = 2 * (size_t)n * sizeof(T) + (size_t)n * sizeof(int);
   if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_gj_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   if (sm > 200 * 1024) throw AcrError(4, "coupling matrix too large");
+  c.kbegin();
   k_gj_inverse<T><<<nb, 256, sm, c.st>>>(n, A, stride, c.d_flag);
-  c.launches++;
+  c.kend(KC_GJ, 2.0 * nb * (double)n * n * n, 2.0 * nb * sizeof(T) * (double)n * n);
   return 0;
 }
 
@@ -195,8 +199,9 @@ template <class T>
 void build_coupling(Ctx& c, int P, int nodes, int K, const T* g, T* Mout) {
   long tot = (long)P * nodes * 4L * K * K;
   if (tot <= 0) return;
+  c.kbegin();
   k_build_coupling<T><<<nblk(tot), 256, 0, c.st>>>(P, nodes, K, g, Mout);
-  c.launches++;
+  c.kend(KC_COPY, 0, (double)sizeof(T) * tot);
 }
 
 // ---- level-0 assembly --------------------------------------------------------
@@ -269,17 +274,19 @@ void assemble_level0(Ctx& c, const Geometry& geo, const double* kappa, double sh
                      const std::vector<const int*>& d_cutq, HMat<T> D, HMat<T> E, HMat<T> F) {
   const int n = geo.n, b = geo.leaf;
   const int nleaf = geo.m / b;
+  c.kbegin();
   k_assemble_leaves<T><<<n * nleaf, std::min(b, 128), 0, c.st>>>(n, b, kappa, shift, d_perm, d_iperm, D.leaf,
                                                                  E.leaf, F.leaf);
-  c.launches++;
+  c.kend(KC_ASSEMBLE, 0, 3.0 * sizeof(T) * (double)geo.m * b * n);
   for (int l = 0; l < geo.L; ++l) {
     int K = geo.ncut[l];
     fill<T>(c, D.U[l], (long)n * D.pps[l], T(0));
     fill<T>(c, D.V[l], (long)n * D.pps[l], T(0));
     long tot = (long)n * (1L << l) * K;
+    c.kbegin();
     k_assemble_cuts<T><<<nblk(tot), 256, 0, c.st>>>(n, 1 << l, K, kappa, d_perm, d_cutp[l], d_cutq[l], D.U[l],
                                                    D.V[l], K, D.pps[l]);
-    c.launches++;
+    c.kend(KC_ASSEMBLE, 0, 4.0 * sizeof(T) * (double)tot);
   }
 }
 
@@ -309,8 +316,9 @@ template <class T>
 void permute_in(Ctx& c, int n, int nrhs, const double* b, long ld, const int* d_perm, T* F) {
   int m = n * n;
   dim3 grid((unsigned)((long)n * ((m + 31) / 32)), (nrhs + 31) / 32);
+  c.kbegin();
   k_permute_in<T><<<grid, dim3(32, 8), 0, c.st>>>(n, nrhs, b, ld, d_perm, F);
-  c.launches++;
+  c.kend(KC_PERMUTE, 0, (8.0 + sizeof(T)) * (double)n * m * nrhs);
 }
 
 template <class T>
@@ -339,8 +347,9 @@ template <class T>
 void permute_out(Ctx& c, int n, int nrhs, const T* F, const int* d_perm, double* x, long ld, int accumulate) {
   int m = n * n;
   dim3 grid((unsigned)((long)n * ((m + 31) / 32)), (nrhs + 31) / 32);
+  c.kbegin();
   k_permute_out<T><<<grid, dim3(32, 8), 0, c.st>>>(n, nrhs, F, d_perm, x, ld, accumulate);
-  c.launches++;
+  c.kend(KC_PERMUTE, 0, (8.0 * (1 + accumulate) + sizeof(T)) * (double)n * m * nrhs);
 }
 
 // ---- FP64 7-point stencil ------------------------------------------------------
@@ -369,8 +378,9 @@ __global__ void k_face_coef(int n, const double* kap, double shift, double* coef
 }
 void face_coefficients(Ctx& c, int n, const double* kappa, double shift, double* coef) {
   long N = (long)n * n * n;
+  c.kbegin();
   k_face_coef<<<nblk(N), 256, 0, c.st>>>(n, kappa, shift, coef);
-  c.launches++;
+  c.kend(KC_STENCIL, 0, 5.0 * 8.0 * N);
 }
 
 // out = alpha * A x + beta * y; optional per-column partial sums of out^2 and y^2.
@@ -435,11 +445,13 @@ void stencil_apply(Ctx& c, int n, int nrhs, const double* coef, const double* x,
   int nb = (int)std::min<long>((N + 255) / 256, 1024);
   double* part = nullptr;
   if (norms_out) part = c.alloc<double>((size_t)nb * nrhs * 2);
+  c.kbegin();
   k_stencil<<<dim3(nb, nrhs), 256, 0, c.st>>>(n, nrhs, coef, x, ld, y, out, alpha, beta, part);
-  c.launches++;
+  c.kend(KC_STENCIL, 13.0 * N * nrhs, 8.0 * (4.0 * N + N * nrhs * (2.0 + (beta != 0.0))));
   if (norms_out) {
+    c.kbegin();
     k_reduce_pairs<<<nrhs, 256, 0, c.st>>>(nrhs, nb, part, norms_out);
-    c.launches++;
+    c.kend(KC_STENCIL, 0, 16.0 * nb * nrhs);
     c.free(part, (size_t)nb * nrhs * 2);
   }
 }
@@ -465,10 +477,15 @@ void col_dots(Ctx& c, long N, int nrhs, const double* x, long ldx, const double*
   int nb = (int)std::min<long>((N + 255) / 256, 512);
   double* part = c.alloc<double>((size_t)nb * nrhs * 2);
   double* pairs = c.alloc<double>((size_t)nrhs * 2);
+  c.kbegin();
   k_col_dots<<<dim3(nb, nrhs), 256, 0, c.st>>>(N, x, ldx, y, ldy, part);
+  c.kend(KC_STENCIL, 2.0 * N * nrhs, 16.0 * N * nrhs);
+  c.kbegin();
   k_reduce_pairs<<<nrhs, 256, 0, c.st>>>(nrhs, nb, part, pairs);
+  c.kend(KC_STENCIL, 0, 16.0 * nb * nrhs);
+  c.kbegin();
   k_copy2d<double><<<1, 64, 0, c.st>>>(1, nrhs, 1, 1.0, pairs, 2, 0, out, 1, 0);
-  c.launches += 3;
+  c.kend(KC_COPY, 0, 16.0 * nrhs);
   c.free(part, (size_t)nb * nrhs * 2);
   c.free(pairs, (size_t)nrhs * 2);
 }
@@ -485,12 +502,14 @@ __global__ void k_col_axpy(long N, int nrhs, const double* a, const double* x, l
   }
 }
 void col_axpy(Ctx& c, long N, int nrhs, const double* a, const double* x, long ldx, double* y, long ldy) {
+  c.kbegin();
   k_col_axpy<<<nblk(N * nrhs), 256, 0, c.st>>>(N, nrhs, a, x, ldx, y, ldy, 0);
-  c.launches++;
+  c.kend(KC_STENCIL, 2.0 * N * nrhs, 24.0 * N * nrhs);
 }
 void col_scale_copy(Ctx& c, long N, int nrhs, const double* a, const double* x, long ldx, double* y, long ldy) {
+  c.kbegin();
   k_col_axpy<<<nblk(N * nrhs), 256, 0, c.st>>>(N, nrhs, a, x, ldx, y, ldy, 1);
-  c.launches++;
+  c.kend(KC_STENCIL, 2.0 * N * nrhs, 24.0 * N * nrhs);
 }
 
 
@@ -516,8 +535,9 @@ void axpy2d(Ctx& c, int P, long rows, int cols, T alpha, const T* src, long sld,
     c.check_range(src, 0, (long)(P - 1) * sps + (rows - 1) * sld + cols - 1, sizeof(T), "axpy2d src");
     c.check_range(dst, 0, (long)(P - 1) * dps + (rows - 1) * dld + cols - 1, sizeof(T), "axpy2d dst");
   }
+  c.kbegin();
   k_axpy2d<T><<<nblk(tot), 256, 0, c.st>>>(P, rows, cols, alpha, src, sld, sps, dst, dld, dps);
-  c.launches++;
+  c.kend(KC_COPY, 0, 3.0 * sizeof(T) * tot);
 }
 
 // Dense m x m image of the leaf blocks of one HODLR matrix (off-diagonal zero).
@@ -533,16 +553,18 @@ __global__ void k_expand_leaves(int m, int b, const T* leaf, T* dense) {
 }
 template <class T>
 void expand_leaves(Ctx& c, int m, int b, const T* leaf, T* dense) {
+  c.kbegin();
   k_expand_leaves<T><<<nblk((long)m * b), 256, 0, c.st>>>(m, b, leaf, dense);
-  c.launches++;
+  c.kend(KC_COPY, 0, 2.0 * sizeof(T) * (double)m * b);
 }
 
 __global__ void k_exp_inplace(double* p, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) p[i] = exp(p[i]);
 }
 void exp_inplace(Ctx& c, double* p, long n) {
+  c.kbegin();
   k_exp_inplace<<<nblk(n), 256, 0, c.st>>>(p, n);
-  c.launches++;
+  c.kend(KC_ASSEMBLE, 0, 16.0 * n);
 }
 
 #define INST(T)                                                                                          \

@@ -624,13 +624,14 @@ int acr_solve_ir(acr_handle h, const double* b, double* x, int nrhs, long ld, do
       stencil_apply(c, h->n, nrhs, h->coef.p, x, ld, b, r.p, -1.0, 1.0, nrm.p);
       ACR_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, c.st));
       ACR_CUDA(cudaStreamSynchronize(c.st));
-      double worst = 0;
+      bool all_ok = true, finite = true;
       for (int k = 0; k < nrhs; ++k) {
-        rel[k] = hn[2 * k + 1] > 0 ? std::sqrt(hn[2 * k] / hn[2 * k + 1]) : 0.0;
-        worst = std::max(worst, rel[k]);
+        rel[k] = hn[2 * k + 1] > 0 ? std::sqrt(hn[2 * k] / hn[2 * k + 1]) : std::sqrt(hn[2 * k]);
+        if (!(rel[k] <= rtol)) all_ok = false;  // NaN counts as not converged
+        if (!std::isfinite(rel[k])) finite = false;
       }
-      if (worst <= rtol) { conv = true; break; }
-      if (!std::isfinite(worst)) break;
+      if (all_ok) { conv = true; break; }
+      if (!finite) break;
     }
     if (it > maxit) it = maxit;
     if (rel_res) std::memcpy(rel_res, rel.data(), nrhs * sizeof(double));
@@ -675,9 +676,10 @@ int acr_solve_fgmres(acr_handle h, const double* b, double* x, int nrhs, long ld
         bn[k] = std::sqrt(hn[2 * k + 1]);
         beta[k] = std::sqrt(hn[2 * k]);
         rel[k] = bn[k] > 0 ? beta[k] / bn[k] : 0;
-        worst = std::max(worst, rel[k]);
+        worst = (rel[k] <= worst) ? worst : rel[k];  // NaN propagates
       }
       if (worst <= rtol) { conv = true; break; }
+      if (!std::isfinite(worst)) break;
       for (int k = 0; k < nrhs; ++k) tmpv[k] = beta[k] > 0 ? 1.0 / beta[k] : 0.0;
       ACR_CUDA(cudaMemcpyAsync(dv.p, tmpv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c.st));
       col_scale_copy(c, N, nrhs, dv.p, Vk(0), N, Vk(0), N);
@@ -728,7 +730,7 @@ int acr_solve_fgmres(acr_handle h, const double* b, double* x, int nrhs, long ld
           gv[(size_t)k * (mrs + 1) + j] = cc * g0;
           gv[(size_t)k * (mrs + 1) + j + 1] = -ss * g0;
           rel[k] = bn[k] > 0 ? std::fabs(gv[(size_t)k * (mrs + 1) + j + 1]) / bn[k] : 0;
-          worst = std::max(worst, rel[k]);
+          worst = (rel[k] <= worst) ? worst : rel[k];
         }
         ACR_CUDA(cudaMemcpyAsync(dv.p, inv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c.st));
         col_scale_copy(c, N, nrhs, dv.p, w.p, N, Vk(j + 1), N);
@@ -758,7 +760,7 @@ int acr_solve_fgmres(acr_handle h, const double* b, double* x, int nrhs, long ld
       double worst = 0;
       for (int k = 0; k < nrhs; ++k) {
         rel[k] = hn[2 * k + 1] > 0 ? std::sqrt(hn[2 * k] / hn[2 * k + 1]) : 0.0;
-        worst = std::max(worst, rel[k]);
+        worst = (rel[k] <= worst) ? worst : rel[k];
       }
       conv = worst <= rtol;
     }

@@ -211,7 +211,10 @@ __global__ void __launch_bounds__(256) k_jacobi(int r, const T* Call, const int*
   const int trans = kL < kR;
   const int nrow = trans ? kR : kL, ncol = trans ? kL : kR;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const T eps = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
+  // Rotate while the pair's cosine exceeds epsrot: 16 u (what the precision can
+  // resolve) or a hundredth of the truncation tolerance, whichever is larger.
+  const T unit = sizeof(T) == 8 ? T(1.1e-16) : T(6e-8);
+  const T eps = fmax(T(16) * unit, T(0.01) * tol);
   if (ncol == 0) {
     if (tid == 0) rankall[bi] = 0;
     for (int i = tid; i < r; i += blockDim.x) sigall[bi * r + i] = T(0);
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(256) k_jacobi(int r, const T* Call, const int*
   T smax = sig[ord[0]];
   int rank = 0;
   if (smax > T(0)) {
-    T thr = fmax(tol * smax, smax * eps * T(4));
+    T thr = fmax(tol * smax, smax * unit * T(4));
     for (int t = 0; t < ncol; ++t) rank += sig[ord[t]] > thr;
   }
   T* X = Xall + bi * (long)r * r;
@@ -420,7 +423,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     c.kbegin();
     k_jacobi<T><<<(unsigned)NB, 256, sm, c.st>>>(r, Cc.p, kk.p, NB, W.p, Vw.p, Xo.p, Yo.p, sig.p, rank.p, T(tol),
-                                                 60);
+                                                 30);
     c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r);
   }
   std::vector<int> hr(NB);

@@ -126,6 +126,36 @@ __global__ void __launch_bounds__(256) k_qr_small(int s, int r, int nclus, long 
   }
 }
 
+// ---- column balancing of the two Gram matrices of a block -------------------
+// M = L R^T is unchanged by L_j *= a_j, R_j /= a_j.  With a_j = sqrt(|R_j|/|L_j|)
+// both factors' columns carry the norm sqrt(|L_j| |R_j|) of their rank-one
+// term, so the pivoted Cholesky thresholds below compare terms by their
+// contribution to M.  Columns with a zero partner are dropped (a = 0).
+template <class T>
+__global__ void k_balance(int r, long NB, T* G, T* aL, T* aR) {
+  const long bi = blockIdx.x;
+  T* GL = G + bi * (long)r * r;
+  T* GR = G + (NB + bi) * (long)r * r;
+  T* al = aL + bi * r;
+  T* ar = aR + bi * r;
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    T nl = sqrt(fmax(GL[(long)j * r + j], T(0))), nr = sqrt(fmax(GR[(long)j * r + j], T(0)));
+    T a = T(0), b = T(0);
+    if (nl > T(0) && nr > T(0)) {
+      a = sqrt(nr / nl);
+      b = T(1) / a;
+    }
+    al[j] = a;
+    ar[j] = b;
+  }
+  __syncthreads();
+  for (long e = threadIdx.x; e < (long)r * r; e += blockDim.x) {
+    int i = (int)(e / r), j = (int)(e % r);
+    GL[e] *= al[i] * al[j];
+    GR[e] *= ar[i] * ar[j];
+  }
+}
+
 // ---- pivoted Cholesky of a Gram matrix --------------------------------------
 // G (r x r, symmetric PSD) ~ P R^T R P^T; R rows t < kk are valid (original
 // column order, zero in already chosen columns), the rest zero.  Stops when
@@ -324,7 +354,7 @@ __global__ void __launch_bounds__(256) k_jacobi(int r, const T* Call, const int*
 template <class T>
 __global__ void __launch_bounds__(256) k_coef(int r, int Kout, long NB, int qr, const T* Rall, const int* pivall,
                                               const int* kkall, const T* Xall, const T* Yall, const T* sigall,
-                                              const int* rankall, T* Zall) {
+                                              const int* rankall, const T* scall, T* Zall) {
   const long j = blockIdx.x;
   const int side = (int)(j / NB);
   const long bi = j % NB;
@@ -348,6 +378,11 @@ __global__ void __launch_bounds__(256) k_coef(int r, int Kout, long NB, int qr, 
         Z[(long)piv[u] * Kout + t] = v / R[(long)u * r + piv[u]];
       }
     }
+  }
+  if (scall) {
+    __syncthreads();
+    const T* sc = scall + j * (long)r;  // side L: aL of block bi; side R: aR (both stored side-major)
+    for (long e = threadIdx.x; e < (long)r * Kout; e += blockDim.x) Z[e] *= sc[e / Kout];
   }
 }
 
@@ -383,6 +418,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     return;
   }
   const bool qr = (s <= 128);
+  DBuf<T> scale;
   DBuf<T> R(c, 2 * NB * r * (size_t)r);
   DBuf<int> piv(c, 2 * NB * (size_t)r), kk(c, 2 * NB);
   if (qr) {
@@ -401,6 +437,10 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
       Op<T> C{G.p + side * NB * r * (long)r, r, 1, (long)nclus * r * r, (long)r * r, 0, 0, 0};
       gemm<T>(c, r, r, s, P, nclus, T(1), A, B, T(0), C);
     }
+    scale = DBuf<T>(c, 2 * NB * (size_t)r);
+    c.kbegin();
+    k_balance<T><<<(unsigned)NB, 256, 0, c.st>>>(r, NB, G.p, scale.p, scale.p + NB * r);
+    c.kend(KC_COPY, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r);
     double epsd = std::max(0.01 * tol * tol, sizeof(T) == 8 ? 1e-15 : 1e-5);
     size_t sm = (size_t)r * sizeof(T);
     if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_pchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -439,7 +479,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
   DBuf<T> Z(c, 2 * NB * (size_t)r * Kout);
   c.kbegin();
   k_coef<T><<<(unsigned)(2 * NB), 256, 0, c.st>>>(r, Kout, NB, qr ? 1 : 0, R.p, piv.p, kk.p, Xo.p, Yo.p, sig.p,
-                                                 rank.p, Z.p);
+                                                 rank.p, scale.p, Z.p);
   c.kend(KC_COEF, 0, 2.0 * NB * sizeof(T) * ((double)r * r + (double)r * Kout));
   Uout = DBuf<T>(c, (size_t)P * m * Kout);
   Vout = DBuf<T>(c, (size_t)P * m * Kout);

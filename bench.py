@@ -197,7 +197,7 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--fp64-compare", type=int, default=1, help="also time one FP64 ACR step (comparator)")
+    ap.add_argument("--fp64-compare", type=int, default=0, help="also time one FP64 ACR step (comparator)")
     ap.add_argument("--ref-budget", type=float, default=20.0, help="seconds of CPU work per oracle sample")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     args = ap.parse_args()

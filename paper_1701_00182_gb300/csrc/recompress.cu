@@ -160,41 +160,57 @@ __global__ void k_balance(int r, long NB, T* G, T* aL, T* aR) {
 // G (r x r, symmetric PSD) ~ P R^T R P^T; R rows t < kk are valid (original
 // column order, zero in already chosen columns), the rest zero.  Stops when
 // the largest remaining diagonal is <= eps * (largest initial diagonal).
+constexpr int kCholThreads = 1024;
 template <class T>
-__global__ void __launch_bounds__(256) k_pchol(int r, const T* Gall, T eps, T* Rall, int* pivall, int* kkall) {
+__global__ void __launch_bounds__(kCholThreads) k_pchol(int r, const T* Gall, T eps, T* Rall, int* pivall,
+                                                        int* kkall) {
   extern __shared__ unsigned char smraw[];
   T* d = reinterpret_cast<T*>(smraw);
-  __shared__ T rv[256];
-  __shared__ int ri[256];
-  __shared__ T s_dmax0;
+  T* colp = d + r;  // R[0..t)[p] of the current pivot column
+  __shared__ T wv[32];
+  __shared__ int wi[32];
+  __shared__ T s_dp, s_dmax0;
+  __shared__ int s_p;
   const long j = blockIdx.x;
   const T* G = Gall + j * (long)r * r;
   T* R = Rall + j * (long)r * r;
   int* piv = pivall + j * r;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int i = tid; i < r; i += blockDim.x) d[i] = fmax(G[(long)i * r + i], T(0));
   __syncthreads();
   int t = 0;
   for (; t < r; ++t) {
     T best = T(-1);
-    int bi = 0;
+    int bi = 0x7fffffff;
     for (int i = tid; i < r; i += blockDim.x)
       if (d[i] > best) { best = d[i]; bi = i; }
-    rv[tid] = best;
-    ri[tid] = bi;
-    __syncthreads();
-    for (int st = 128; st > 0; st >>= 1) {
-      if (tid < st && (rv[tid + st] > rv[tid] || (rv[tid + st] == rv[tid] && ri[tid + st] < ri[tid]))) {
-        rv[tid] = rv[tid + st];
-        ri[tid] = ri[tid + st];
-      }
-      __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
-    const T dp = rv[0];
-    const int p = ri[0];
-    if (t == 0 && tid == 0) s_dmax0 = dp;
+    if (lane == 0) { wv[warp] = best; wi[warp] = bi; }
     __syncthreads();
+    if (warp == 0) {
+      best = lane < nw ? wv[lane] : T(-1);
+      bi = lane < nw ? wi[lane] : 0x7fffffff;
+      for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        s_dp = best;
+        s_p = bi;
+        if (t == 0) s_dmax0 = best;
+      }
+    }
+    __syncthreads();
+    const T dp = s_dp;
+    const int p = s_p;
     if (!(dp > eps * s_dmax0) || !(dp > T(0))) break;
+    for (int u = tid; u < t; u += blockDim.x) colp[u] = R[(long)u * r + p];
+    __syncthreads();
     const T sq = sqrt(dp), isq = T(1) / sq;
     for (int i = tid; i < r; i += blockDim.x) {
       T v;
@@ -204,15 +220,12 @@ __global__ void __launch_bounds__(256) k_pchol(int r, const T* Gall, T eps, T* R
         v = sq;
       } else {
         v = G[(long)p * r + i];
-        for (int u = 0; u < t; ++u) v -= R[(long)u * r + p] * R[(long)u * r + i];
+        for (int u = 0; u < t; ++u) v -= colp[u] * R[(long)u * r + i];
         v *= isq;
       }
       R[(long)t * r + i] = v;
-    }
-    __syncthreads();
-    for (int i = tid; i < r; i += blockDim.x) {
       if (i == p) d[i] = T(-1);
-      else if (d[i] >= T(0)) d[i] = fmax(d[i] - R[(long)t * r + i] * R[(long)t * r + i], T(0));
+      else if (d[i] >= T(0)) d[i] = fmax(d[i] - v * v, T(0));
     }
     if (tid == 0) piv[t] = p;
     __syncthreads();
@@ -224,24 +237,31 @@ __global__ void __launch_bounds__(256) k_pchol(int r, const T* Gall, T eps, T* R
 // ---- one-sided Jacobi SVD of the core ----------------------------------------
 // C (row major, valid kL x kR) = X diag(sig) Y^T, sig sorted descending.
 // X[i][t] (i < kL) and Y[i][t] (i < kR) row major with leading dimension r;
-// rank = #{sig > tol sig_1}.
+// rank = #{sig > tol sig_1}.  The wider side is orthogonalised column by
+// column (Hestenes), with a round-robin tournament so the ncol/2 disjoint
+// pairs of a step run on separate warps.  The working matrix lives in shared
+// memory when it fits (ldw = nrow), otherwise in the global work buffer.
+constexpr int kJacThreads = 1024;
 template <class T>
-__global__ void __launch_bounds__(256) k_jacobi(int r, const T* Call, const int* kk, long NB, T* Wall, T* Vall,
-                                                T* Xall, T* Yall, T* sigall, int* rankall, T tol, int maxsweeps) {
+__global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, const int* kk, long NB, T* Wall, T* Vall,
+                                                        T* Xall, T* Yall, T* sigall, int* rankall, T tol,
+                                                        int maxsweeps, int smem_elems) {
   extern __shared__ unsigned char smraw[];
   T* sig = reinterpret_cast<T*>(smraw);
   int* ord = reinterpret_cast<int*>(sig + r);
+  T* Ws = reinterpret_cast<T*>(ord + r + (r & 1));
   __shared__ int s_rot;
-  __shared__ T red[32];
   const long bi = blockIdx.x;
   const T* C = Call + bi * (long)r * r;
-  T* W = Wall + bi * (long)r * r;  // column major, ld r
-  T* V = Vall + bi * (long)r * r;
   const int kL = kk[bi], kR = kk[NB + bi];
   const int trans = kL < kR;
   const int nrow = trans ? kR : kL, ncol = trans ? kL : kR;
+  const bool insm = (long)nrow * ncol <= smem_elems;
+  const long ldw = insm ? nrow : r;
+  T* W = insm ? Ws : Wall + bi * (long)r * r;  // column major
+  T* V = Vall + bi * (long)r * r;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  // Rotate while the pair's cosine exceeds epsrot: 16 u (what the precision can
+  // Rotate while the pair's cosine exceeds eps: 16 u (what the precision can
   // resolve) or a hundredth of the truncation tolerance, whichever is larger.
   const T unit = sizeof(T) == 8 ? T(1.1e-16) : T(6e-8);
   const T eps = fmax(T(16) * unit, T(0.01) * tol);
@@ -252,7 +272,7 @@ __global__ void __launch_bounds__(256) k_jacobi(int r, const T* Call, const int*
   }
   for (long e = tid; e < (long)nrow * ncol; e += blockDim.x) {
     int row = (int)(e % nrow), col = (int)(e / nrow);
-    W[(long)col * r + row] = trans ? C[(long)col * r + row] : C[(long)row * r + col];
+    W[(long)col * ldw + row] = trans ? C[(long)col * r + row] : C[(long)row * r + col];
   }
   for (long e = tid; e < (long)ncol * ncol; e += blockDim.x) {
     int row = (int)(e % ncol), col = (int)(e / ncol);
@@ -274,8 +294,8 @@ __global__ void __launch_bounds__(256) k_jacobi(int r, const T* Call, const int*
           jx = 1 + ((step - k) % (ne - 1) + (ne - 1)) % (ne - 1);
         }
         if (i >= ncol || jx >= ncol) continue;
-        T* wi = W + (long)i * r;
-        T* wj = W + (long)jx * r;
+        T* wi = W + (long)i * ldw;
+        T* wj = W + (long)jx * ldw;
         T a = 0, b = 0, g = 0;
         for (int q = lane; q < nrow; q += 32) {
           T x = wi[q], y = wj[q];
@@ -313,7 +333,7 @@ __global__ void __launch_bounds__(256) k_jacobi(int r, const T* Call, const int*
   }
   for (int col = warp; col < ncol; col += nw) {
     T a = 0;
-    for (int q = lane; q < nrow; q += 32) a += W[(long)col * r + q] * W[(long)col * r + q];
+    for (int q = lane; q < nrow; q += 32) a += W[(long)col * ldw + q] * W[(long)col * ldw + q];
     a = warp_sum(a);
     if (lane == 0) sig[col] = sqrt(a);
   }
@@ -337,7 +357,7 @@ __global__ void __launch_bounds__(256) k_jacobi(int r, const T* Call, const int*
     int t = (int)(e / r), i = (int)(e % r);
     int col = ord[t];
     T sc = sig[col];
-    T wv = (i < nrow) ? W[(long)col * r + i] / sc : T(0);
+    T wv = (i < nrow) ? W[(long)col * ldw + i] / sc : T(0);
     T vv = (i < ncol) ? V[(long)col * r + i] : T(0);
     // !trans: X = W/s (kL = nrow rows), Y = V (kR = ncol rows); trans: swapped.
     X[(long)i * r + t] = trans ? vv : wv;
@@ -442,10 +462,10 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     k_balance<T><<<(unsigned)NB, 256, 0, c.st>>>(r, NB, G.p, scale.p, scale.p + NB * r);
     c.kend(KC_COPY, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r);
     double epsd = std::max(0.01 * tol * tol, sizeof(T) == 8 ? 1e-15 : 1e-5);
-    size_t sm = (size_t)r * sizeof(T);
+    size_t sm = 2 * (size_t)r * sizeof(T);
     if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_pchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     c.kbegin();
-    k_pchol<T><<<(unsigned)(2 * NB), 256, sm, c.st>>>(r, G.p, T(epsd), R.p, piv.p, kk.p);
+    k_pchol<T><<<(unsigned)(2 * NB), kCholThreads, sm, c.st>>>(r, G.p, T(epsd), R.p, piv.p, kk.p);
     c.kend(KC_PCHOL, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r);
   }
   DBuf<T> Cc(c, NB * (size_t)r * r);
@@ -459,11 +479,15 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
       Yo(c, NB * (size_t)r * r), sig(c, NB * (size_t)r);
   DBuf<int> rank(c, NB);
   {
-    size_t sm = (size_t)r * (sizeof(T) + sizeof(int));
-    if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    size_t base = (size_t)r * (sizeof(T) + sizeof(int)) + ((r & 1) ? sizeof(int) : 0);
+    base = (base + 15) / 16 * 16;
+    const size_t cap = 200 * 1024;
+    int smem_elems = (int)std::min<size_t>((size_t)r * r, cap > base ? (cap - base) / sizeof(T) : 0);
+    size_t sm = base + (size_t)smem_elems * sizeof(T);
+    ACR_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     c.kbegin();
-    k_jacobi<T><<<(unsigned)NB, 256, sm, c.st>>>(r, Cc.p, kk.p, NB, W.p, Vw.p, Xo.p, Yo.p, sig.p, rank.p, T(tol),
-                                                 30);
+    k_jacobi<T><<<(unsigned)NB, kJacThreads, sm, c.st>>>(r, Cc.p, kk.p, NB, W.p, Vw.p, Xo.p, Yo.p, sig.p, rank.p,
+                                                         T(tol), 30, smem_elems);
     c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r);
   }
   std::vector<int> hr(NB);

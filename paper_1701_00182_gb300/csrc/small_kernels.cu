@@ -80,48 +80,59 @@ void set_identity_clusters(Ctx& c, int P, int m, int s, T* U, long ld, long ps) 
 // matrix of order n (row major, matrices `stride` elements apart).  A pivot
 // below 64 u max|A| sets flag[0] = 1 and is replaced by that threshold so the
 // kernel always finishes.
+constexpr int kGJThreads = 1024;
 template <class T>
-__global__ void __launch_bounds__(256) k_gj_inverse(int n, T* A, long stride, int* flag) {
+__device__ __forceinline__ void argmax_shfl(T& v, int& i) {
+  for (int o = 16; o > 0; o >>= 1) {
+    T ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+  }
+}
+template <class T>
+__global__ void __launch_bounds__(kGJThreads) k_gj_inverse(int n, T* A, long stride, int* flag) {
   extern __shared__ unsigned char smraw[];
   T* rowk = reinterpret_cast<T*>(smraw);
   T* fcol = rowk + n;
   int* piv = reinterpret_cast<int*>(fcol + n);
-  __shared__ T redv[256];
-  __shared__ int redi[256];
+  __shared__ T wv[32];
+  __shared__ int wi[32];
   __shared__ T s_thr;
+  __shared__ int s_p;
   T* a = A + (long)blockIdx.x * stride;
-  const int tid = threadIdx.x;
-  // max |A| for the breakdown threshold
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   T mx = T(0);
   for (long e = tid; e < (long)n * n; e += blockDim.x) mx = fmax(mx, fabs(a[e]));
-  redv[tid] = mx;
+  int dummy = 0;
+  argmax_shfl(mx, dummy);
+  if (lane == 0) wv[warp] = mx;
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (tid < s) redv[tid] = fmax(redv[tid], redv[tid + s]);
-    __syncthreads();
+  if (tid == 0) {
+    T m2 = T(0);
+    for (int w = 0; w < nw; ++w) m2 = fmax(m2, wv[w]);
+    const T eps = sizeof(T) == 8 ? T(1.1e-16) : T(6e-8);
+    s_thr = m2 > T(0) ? T(64) * eps * m2 : T(1e-30);
   }
-  const T eps = sizeof(T) == 8 ? T(1.1e-16) : T(6e-8);
-  if (tid == 0) s_thr = redv[0] > T(0) ? T(64) * eps * redv[0] : T(1e-30);
   __syncthreads();
   const T thr = s_thr;
   for (int k = 0; k < n; ++k) {
     T best = T(-1);
-    int bi = k;
+    int bi = 0x7fffffff;
     for (int i = k + tid; i < n; i += blockDim.x) {
       T v = fabs(a[(long)i * n + k]);
       if (v > best) { best = v; bi = i; }
     }
-    redv[tid] = best;
-    redi[tid] = bi;
+    argmax_shfl(best, bi);
+    if (lane == 0) { wv[warp] = best; wi[warp] = bi; }
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-      if (tid < s && (redv[tid + s] > redv[tid] || (redv[tid + s] == redv[tid] && redi[tid + s] < redi[tid]))) {
-        redv[tid] = redv[tid + s];
-        redi[tid] = redi[tid + s];
-      }
-      __syncthreads();
+    if (warp == 0) {
+      best = lane < nw ? wv[lane] : T(-1);
+      bi = lane < nw ? wi[lane] : 0x7fffffff;
+      argmax_shfl(best, bi);
+      if (lane == 0) s_p = (bi < n) ? bi : k;
     }
-    const int p = redi[0];
+    __syncthreads();
+    const int p = s_p;
     if (tid == 0) piv[k] = p;
     if (p != k) {
       for (int j = tid; j < n; j += blockDim.x) {
@@ -171,7 +182,8 @@ int batched_inverse(Ctx& c, int nb, int n, T* A, long stride) {
   if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_gj_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   if (sm > 200 * 1024) throw AcrError(4, "coupling matrix too large");
   c.kbegin();
-  k_gj_inverse<T><<<nb, 256, sm, c.st>>>(n, A, stride, c.d_flag);
+  const int thr = n <= 64 ? 256 : kGJThreads;
+  k_gj_inverse<T><<<nb, thr, sm, c.st>>>(n, A, stride, c.d_flag);
   c.kend(KC_GJ, 2.0 * nb * (double)n * n * n, 2.0 * nb * sizeof(T) * (double)n * n);
   return 0;
 }

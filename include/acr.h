@@ -86,6 +86,7 @@ typedef struct {
   double kc_flops[16];
   double kc_bytes[16];
   long long kc_launches[16];
+  int jacobi_sweeps_max;                  /* most Jacobi sweeps any core SVD of the factorisation needed */
 } acr_stats;
 
 /* Default options (FP64, shift 0, unlimited ranks and memory, autotune off, nrhs_max 64). */

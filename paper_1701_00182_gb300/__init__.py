@@ -67,6 +67,7 @@ class AcrStats(C.Structure):
         ("kc_flops", C.c_double * 16),
         ("kc_bytes", C.c_double * 16),
         ("kc_launches", C.c_longlong * 16),
+        ("jacobi_sweeps_max", C.c_int),
     ]
 
 
@@ -278,6 +279,7 @@ def acr_get_stats(h: Handle) -> dict:
         "factor_bytes": s.factor_bytes, "peak_bytes": s.peak_bytes, "t_factor_ms": s.t_factor_ms,
         "t_level_ms": [s.t_level_ms[r] for r in range(min(q, 16))], "gemm_flops": s.gemm_flops,
         "kernel_launches": s.kernel_launches,
+        "jacobi_sweeps_max": s.jacobi_sweeps_max,
         "kernels": {nm: {"ms": s.kc_ms[i], "flops": s.kc_flops[i], "bytes": s.kc_bytes[i],
                          "launches": s.kc_launches[i]} for i, nm in enumerate(KERNEL_CLASSES)},
     }

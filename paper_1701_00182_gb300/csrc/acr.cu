@@ -68,7 +68,8 @@ void Ctx::kend(int cls, double flops, double bytes) {
   cudaEvent_t b = evfree.back();
   evfree.pop_back();
   ACR_CUDA(cudaEventRecord(b, st));
-  pend.push_back({evcur, b, cls});
+  pend.push_back({evcur, b, cls, cls == KC_GEMM ? tag : nullptr});
+  if (cls == KC_GEMM) site[tag].second += flops;
   evcur = nullptr;
   if (pend.size() >= 8192) kflush();
 }
@@ -78,7 +79,10 @@ void Ctx::kflush() {
   ACR_CUDA(cudaStreamSynchronize(st));
   for (auto& p : pend) {
     float ms = 0;
-    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) kc_ms[p.cls] += ms;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      kc_ms[p.cls] += ms;
+      if (p.tag) site[p.tag].first += ms;
+    }
     evfree.push_back(p.a);
     evfree.push_back(p.b);
   }
@@ -158,6 +162,13 @@ struct acr_handle_s {
     coef.release();
     if (ctx.d_flag) cudaFree(ctx.d_flag);
     if (ctx.st) cudaStreamSynchronize(ctx.st);
+    const char* ps = std::getenv("ACR_PROFILE_SITES");
+    if (ps && ps[0] == '1' && !ctx.site.empty()) {
+      ctx.kflush();
+      for (auto& kv : ctx.site)
+        std::fprintf(stderr, "acr gemm site %-14s %10.1f ms %10.3f TFLOP\n", kv.first.c_str(), kv.second.first,
+                     kv.second.second / 1e12);
+    }
     for (auto& p : ctx.pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : ctx.evfree) cudaEventDestroy(e);
     if (ctx.st) cudaStreamSynchronize(ctx.st);
@@ -184,9 +195,11 @@ int guard(Fn&& fn) {
 }
 
 void check_flag(acr_handle_s* h) {
-  int f = 0;
-  ACR_CUDA(cudaMemcpyAsync(&f, h->ctx.d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->ctx.st));
+  int fl[4] = {0, 0, 0, 0};
+  ACR_CUDA(cudaMemcpyAsync(fl, h->ctx.d_flag, sizeof(fl), cudaMemcpyDeviceToHost, h->ctx.st));
   ACR_CUDA(cudaStreamSynchronize(h->ctx.st));
+  h->stats.jacobi_sweeps_max = fl[1];
+  const int f = fl[0];
   if (f) {
     ACR_CUDA(cudaMemsetAsync(h->ctx.d_flag, 0, sizeof(int), h->ctx.st));
     throw AcrError(ACR_ERR_BREAKDOWN, "zero pivot in a leaf or coupling inverse");
@@ -487,8 +500,8 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     c.check_bounds = cb && cb[0] == '1';
     c.autotune = o.autotune != 0;
     c.profile = o.profile != 0;
-    ACR_CUDA(cudaMalloc(&c.d_flag, sizeof(int)));
-    ACR_CUDA(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.st));
+    ACR_CUDA(cudaMalloc(&c.d_flag, 4 * sizeof(int)));
+    ACR_CUDA(cudaMemsetAsync(c.d_flag, 0, 4 * sizeof(int), c.st));
     h->n = n;
     h->leaf = leaf;
     h->tol = tol;

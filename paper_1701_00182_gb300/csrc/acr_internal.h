@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <map>
+#include <string>
 #include <cstdio>
 #include <stdexcept>
 #include <string>
@@ -57,7 +58,9 @@ struct Ctx {
   bool profile = false;  // record CUDA events around every launch, accumulated per kernel class
   double kc_ms[16] = {}, kc_flops[16] = {}, kc_bytes[16] = {};
   long long kc_launch[16] = {};
-  struct PendingEv { cudaEvent_t a, b; int cls; };
+  struct PendingEv { cudaEvent_t a, b; int cls; const char* tag; };
+  const char* tag = "other";  // call site of the next GEMM (profile breakdown)
+  std::map<std::string, std::pair<double, double>> site;  // tag -> (ms, flops)
   std::vector<cudaEvent_t> evfree;
   std::vector<PendingEv> pend;
   cudaEvent_t evcur = nullptr;

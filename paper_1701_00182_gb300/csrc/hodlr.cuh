@@ -43,6 +43,7 @@ template <class T>
 void hmatvec(Ctx& c, const HMat<T>& A, int lmin, bool trans, Pan<T> W, Pan<T> Y, int w, T alpha, T beta) {
   const int P = A.P, m = A.m, b = A.b, nleaf = m / b;
   if (P <= 0 || w <= 0) return;
+  c.tag = "mv_leaf";
   gemm<T>(c, b, w, b, P, nleaf, alpha, opm<T>(A.leaf, trans ? 1 : b, trans ? b : 1, A.lps, (long)b * b),
           opm<T>(W.p, W.ld, 1, W.ps, (long)b * W.ld), beta, opm<T>(Y.p, Y.ld, 1, Y.ps, (long)b * Y.ld));
   for (int l = std::max(lmin, 0); l < A.L; ++l) {
@@ -52,8 +53,10 @@ void hmatvec(Ctx& c, const HMat<T>& A, int lmin, bool trans, Pan<T> W, Pan<T> Y,
     T* Cf = trans ? A.U[l] : A.V[l];
     T* Ex = trans ? A.V[l] : A.U[l];
     DBuf<T> cb(c, (size_t)P * nclus * K * w);
+    c.tag = "mv_coef";
     gemm<T>(c, K, w, s, P, nclus, T(1), opm<T>(Cf, 1, K, A.pps[l], (long)s * K),
             opm<T>(W.p, W.ld, 1, W.ps, (long)s * W.ld), T(0), opm<T>(cb.p, w, 1, (long)nclus * K * w, (long)K * w));
+    c.tag = "mv_expand";
     gemm<T>(c, s, w, K, P, nclus, alpha, opm<T>(Ex, K, 1, A.pps[l], (long)s * K),
             opm<T>(cb.p, w, 1, (long)nclus * K * w, (long)K * w, 1), T(1),
             opm<T>(Y.p, Y.ld, 1, Y.ps, (long)s * Y.ld));
@@ -75,6 +78,7 @@ struct WSum {
 template <class T>
 void wsum_apply(Ctx& c, const WSum<T>& X, int lmin, bool trans, Pan<T> W, Pan<T> Y, int w) {
   const int P = X.P, m = X.m, b = X.b, nleaf = m / b;
+  c.tag = "ws_leaf";
   gemm<T>(c, b, w, b, P, nleaf, T(1), opm<T>(X.leafinv.p, trans ? 1 : b, trans ? b : 1, (long)m * b, (long)b * b),
           opm<T>(W.p, W.ld, 1, W.ps, (long)b * W.ld), T(0), opm<T>(Y.p, Y.ld, 1, Y.ps, (long)b * Y.ld));
   for (int l = lmin; l < X.L; ++l) {
@@ -83,12 +87,15 @@ void wsum_apply(Ctx& c, const WSum<T>& X, int lmin, bool trans, Pan<T> W, Pan<T>
     T* first = trans ? X.Pc[l].p : X.Qc[l].p;
     T* second = trans ? X.Qc[l].p : X.Pc[l].p;
     DBuf<T> cb(c, (size_t)P * nclus * K * w), db(c, (size_t)P * nclus * K * w);
+    c.tag = "ws_coef";
     gemm<T>(c, K, w, s, P, nclus, T(1), opm<T>(first, 1, K, (long)m * K, (long)s * K),
             opm<T>(W.p, W.ld, 1, W.ps, (long)s * W.ld), T(0), opm<T>(cb.p, w, 1, (long)nclus * K * w, (long)K * w));
     const long K2 = 2L * K;
+    c.tag = "ws_kmix";
     gemm<T>(c, (int)K2, w, (int)K2, P, nodes, T(1),
             opm<T>(X.Kp[l].p, trans ? 1 : K2, trans ? K2 : 1, (long)nodes * K2 * K2, K2 * K2),
             opm<T>(cb.p, w, 1, (long)nclus * K * w, K2 * w), T(0), opm<T>(db.p, w, 1, (long)nclus * K * w, K2 * w));
+    c.tag = "ws_expand";
     gemm<T>(c, s, w, K, P, nclus, T(-1), opm<T>(second, K, 1, (long)m * K, (long)s * K),
             opm<T>(db.p, w, 1, (long)nclus * K * w, (long)K * w), T(1), opm<T>(Y.p, Y.ld, 1, Y.ps, (long)s * Y.ld));
   }
@@ -113,6 +120,7 @@ WSum<T> winverse(Ctx& c, const HMat<T>& D) {
     wsum_apply<T>(c, X, l + 1, false, Pan<T>{D.U[l], K, D.pps[l]}, Pan<T>{X.Pc[l].p, K, (long)m * K}, K);
     wsum_apply<T>(c, X, l + 1, true, Pan<T>{D.V[l], K, D.pps[l]}, Pan<T>{X.Qc[l].p, K, (long)m * K}, K);
     DBuf<T> g(c, (size_t)P * nclus * K * K);
+    c.tag = "inv_g";
     gemm<T>(c, K, K, s, P, nclus, T(1), opm<T>(D.V[l], 1, K, D.pps[l], (long)s * K),
             opm<T>(X.Pc[l].p, K, 1, (long)m * K, (long)s * K), T(0),
             opm<T>(g.p, K, 1, (long)nclus * K * K, (long)K * K));
@@ -149,9 +157,11 @@ HStore<T> wsum_to_hodlr(Ctx& c, WSum<T>& X, double tol, bool exact, int* ranks_o
     const long K2 = 2L * K;
     Z[l] = DBuf<T>(c, (size_t)P * m * K);
     // Z = P ~ Kinv[a][a] of the row's level-(l+1) child a (diagonal block of the swapped inverse)
+    c.tag = "conv_z";
     gemm<T>(c, s, K, K, P, nclus, T(1), opm<T>(X.Pc[l].p, K, 1, (long)m * K, (long)s * K),
             opm<T>(X.Kp[l].p, K2, 1, (long)nodes * K2 * K2, K2 * K2, 0, 1, K2 * K + K), T(0),
             opm<T>(Z[l].p, K, 1, (long)m * K, (long)s * K));
+    c.tag = "conv_leaf";
     gemm<T>(c, b, b, K, P, nleaf, T(-1), opm<T>(Z[l].p, K, 1, (long)m * K, (long)b * K),
             opm<T>(X.Qc[l].p, 1, K, (long)m * K, (long)b * K), T(1), opm<T>(out.leaf.p, b, 1, (long)m * b, (long)b * b));
   }
@@ -167,6 +177,7 @@ HStore<T> wsum_to_hodlr(Ctx& c, WSum<T>& X, double tol, bool exact, int* ranks_o
       if (X.have[l0]) {
         const int K = X.K[l0], s = m >> (l0 + 1), nclus = 1 << (l0 + 1), nodes = nclus / 2;
         const long K2 = 2L * K;
+        c.tag = "conv_own";
         gemm<T>(c, s, K, K, P, nclus, T(-1), opm<T>(X.Pc[l0].p, K, 1, (long)m * K, (long)s * K),
                 opm<T>(X.Kp[l0].p + K, K2, 1, (long)nodes * K2 * K2, K2 * K2, 0, 1, K2 * K - K), T(0),
                 opm<T>(Lf.p, r, 1, (long)m * r, (long)s * r));
@@ -246,21 +257,25 @@ void flat_add_product(Ctx& c, Flat<T>& F, const HMat<T>& A, const HMat<T>& B, T 
     }
     if (KA > 0 && KB > 0) {
       DBuf<T> Tb(c, (size_t)Pb * nclus * KA * KB);
+      c.tag = "prod_T";
       gemm<T>(c, KA, KB, s, Pb, nclus, T(1), opm<T>(A.V[l], 1, KA, A.pps[l], (long)s * KA, 1),
               opm<T>(B.U[l], KB, 1, B.pps[l], (long)s * KB, 1), T(0),
               opm<T>(Tb.p, KB, 1, (long)nclus * KA * KB, (long)KA * KB));
       F.owned.emplace_back(c, (size_t)Pb * m * KB);
       Wl[l] = F.owned.back().p;
+      c.tag = "prod_W";
       gemm<T>(c, s, KB, KA, Pb, nclus, T(1), opm<T>(A.U[l], KA, 1, A.pps[l], (long)s * KA),
               opm<T>(Tb.p, KB, 1, (long)nclus * KA * KB, (long)KA * KB), T(0),
               opm<T>(Wl[l], KB, 1, (long)m * KB, (long)s * KB));
     }
   }
+  c.tag = "prod_leaf";
   gemm<T>(c, b, b, b, Pb, nleaf, coef, opm<T>(A.leaf, b, 1, A.lps, (long)b * b),
           opm<T>(B.leaf, b, 1, B.lps, (long)b * b), T(1), opm<T>(F.leaf.p, b, 1, (long)m * b, (long)b * b));
   for (int l = 0; l < L; ++l) {
     if (!Wl[l]) continue;
     const int KB = B.K[l];
+    c.tag = "prod_leafW";
     gemm<T>(c, b, b, KB, Pb, nleaf, coef, opm<T>(Wl[l], KB, 1, (long)m * KB, (long)b * KB),
             opm<T>(B.V[l], 1, KB, B.pps[l], (long)b * KB), T(1), opm<T>(F.leaf.p, b, 1, (long)m * b, (long)b * b));
   }

@@ -245,7 +245,7 @@ constexpr int kJacThreads = 1024;
 template <class T>
 __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, const int* kk, long NB, T* Wall, T* Vall,
                                                         T* Xall, T* Yall, T* sigall, int* rankall, T tol,
-                                                        int maxsweeps, int smem_elems) {
+                                                        int maxsweeps, int smem_elems, int* sweeps_out) {
   extern __shared__ unsigned char smraw[];
   T* sig = reinterpret_cast<T*>(smraw);
   int* ord = reinterpret_cast<int*>(sig + r);
@@ -263,8 +263,10 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   // Rotate while the pair's cosine exceeds eps: 16 u (what the precision can
   // resolve) or a hundredth of the truncation tolerance, whichever is larger.
+  // The cosine of two columns is only known to about u sqrt(nrow), so the
+  // threshold never goes below 4 u sqrt(nrow).
   const T unit = sizeof(T) == 8 ? T(1.1e-16) : T(6e-8);
-  const T eps = fmax(T(16) * unit, T(0.01) * tol);
+  const T eps = fmax(T(4) * unit * sqrt(T(nrow > 16 ? nrow : 16)), T(0.01) * tol);
   if (ncol == 0) {
     if (tid == 0) rankall[bi] = 0;
     for (int i = tid; i < r; i += blockDim.x) sigall[bi * r + i] = T(0);
@@ -329,6 +331,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
     }
     const int rot = s_rot;
     __syncthreads();
+    if (tid == 0 && sweeps_out) atomicMax(sweeps_out, sw + 1);
     if (!rot) break;
   }
   for (int col = warp; col < ncol; col += nw) {
@@ -426,6 +429,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     Op<T> A{Rb.p, r, 1, (long)m * r, (long)s * r, 0, 0, 1};
     Op<T> B{Lb.p, 1, r, (long)m * r, (long)s * r, 0, 0, 0};
     Op<T> C{V2.p, s, 1, (long)m * s, (long)s * s, 0, 0, 1};
+    c.tag = "densify";
     gemm<T>(c, s, s, r, P, nclus, T(1), A, B, T(0), C);
     Lb = std::move(U2);
     Rb = std::move(V2);
@@ -455,6 +459,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
       Op<T> A{F, 1, r, (long)m * r, (long)s * r, 0, 0, side};
       Op<T> B{F, r, 1, (long)m * r, (long)s * r, 0, 0, side};
       Op<T> C{G.p + side * NB * r * (long)r, r, 1, (long)nclus * r * r, (long)r * r, 0, 0, 0};
+      c.tag = "gram";
       gemm<T>(c, r, r, s, P, nclus, T(1), A, B, T(0), C);
     }
     scale = DBuf<T>(c, 2 * NB * (size_t)r);
@@ -473,6 +478,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     Op<T> A{R.p, r, 1, 0, (long)r * r, 0, 0, 0};
     Op<T> B{R.p + NB * r * (long)r, 1, r, 0, (long)r * r, 0, 0, 0};
     Op<T> C{Cc.p, r, 1, 0, (long)r * r, 0, 0, 0};
+    c.tag = "core";
     gemm<T>(c, r, r, r, 1, (int)NB, T(1), A, B, T(0), C);
   }
   DBuf<T> W(c, NB * (size_t)r * r), Vw(c, NB * (size_t)r * r), Xo(c, NB * (size_t)r * r),
@@ -487,7 +493,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     ACR_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     c.kbegin();
     k_jacobi<T><<<(unsigned)NB, kJacThreads, sm, c.st>>>(r, Cc.p, kk.p, NB, W.p, Vw.p, Xo.p, Yo.p, sig.p, rank.p,
-                                                         T(tol), 30, smem_elems);
+                                                         T(tol), 30, smem_elems, c.d_flag + 1);
     c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r);
   }
   std::vector<int> hr(NB);
@@ -512,6 +518,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     Op<T> A{F, r, 1, (long)m * r, (long)s * r, 0, 0, 0};
     Op<T> B{Z.p + side * NB * r * (long)Kout, Kout, 1, (long)nclus * r * Kout, (long)r * Kout, 0, 0, side};
     Op<T> C{(side ? Vout.p : Uout.p), Kout, 1, (long)m * Kout, (long)s * Kout, 0, 0, 0};
+    c.tag = "rebuild";
     gemm<T>(c, s, Kout, r, P, nclus, T(1), A, B, T(0), C);
   }
 }

@@ -1,0 +1,89 @@
+"""The benchmark's workload configurations, run through the C ABI and checked
+with the oracle: the operator residual is exact at any size, and at n = 64 the
+oracle's FP64 Krylov solution is the reference."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import iterative
+
+from gpu_util import empty_like_cols, from_cols, rel, to_cols
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def acr():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1701_00182_gb300 import build as b
+
+    b.build()
+    import paper_1701_00182_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def grf64():
+    n = 64
+    g = synthetic.gaussian_random_field(n, 1)
+    f = synthetic.uniform_rhs(n, 2)
+    ref = iterative.reference_solve(n, g, f, rtol=1e-13)
+    return n, g, f, ref
+
+
+def test_variable_coefficient_n64_fp64_direct(acr, grf64):
+    """FP64 ACR as a direct solver: within 10x the truncation tolerance."""
+    n, g, f, ref = grf64
+    h = acr.acr_factor(n, g, 1e-6, 64)
+    b = to_cols(f)
+    x = empty_like_cols(b)
+    acr.acr_solve(h, b, x)
+    assert rel(from_cols(x)[:, 0], ref) < 1e-5
+
+
+def test_variable_coefficient_n64_fp32_refined(acr, grf64):
+    """FP32 ACR + FP64 refinement to 1e-10, checked with the oracle's operator."""
+    n, g, f, ref = grf64
+    h = acr.acr_factor(n, g, 1e-6, 64, precision=acr.ACR_FP32)
+    b = to_cols(f)
+    x = empty_like_cols(b)
+    it, relr, _ = acr.acr_solve_ir(h, b, x, rtol=1e-10, maxit=40)
+    u = from_cols(x)[:, 0]
+    assert iterative.rel_residual(n, g, u, f)[0] <= 1.01e-10
+    assert rel(u, ref) < 1e-8
+
+
+def test_helmholtz_n64_fgmres_ranks(acr):
+    n = 64
+    w = synthetic.helmholtz_omega(n)
+    f = synthetic.point_source(n, 3)
+    h = acr.acr_factor(n, None, 1e-4, 64, precision=acr.ACR_FP32, shift=-w * w)
+    b = to_cols(f)
+    x = empty_like_cols(b)
+    it, relr, _ = acr.acr_solve_fgmres(h, b, x, rtol=1e-10, restart=50, maxit=400)
+    u = from_cols(x)[:, 0]
+    assert iterative.rel_residual(n, None, u, f, shift=-w * w)[0] <= 1.01e-10
+    s = acr.acr_get_stats(h)
+    assert len(s["max_rank"]) == s["levels_cr"] + 1
+    assert all(len(row) == s["levels_h"] for row in s["max_rank"])
+
+
+def test_full_size_multi_rhs_sampled(acr):
+    """n = 128, 64 RHS, FP32 ACR + FP64 refinement (the benchmark's step);
+    three sampled columns are re-checked on the CPU with the oracle's operator."""
+    import torch
+
+    n = 128
+    g = synthetic.gaussian_random_field(n, 1)
+    F = synthetic.multi_rhs(n, range(100, 164))
+    h = acr.acr_factor(n, torch.from_numpy(g).cuda(), 1e-6, 64, precision=acr.ACR_FP32)
+    b = to_cols(F)
+    x = empty_like_cols(b)
+    it, relr, _ = acr.acr_solve_ir(h, b, x, rtol=1e-10, maxit=60)
+    assert np.all(relr <= 1e-10)
+    X = from_cols(x)
+    for c in (0, 31, 63):
+        assert iterative.rel_residual(n, g, X[:, c], F[:, c])[0] <= 1.01e-10

@@ -134,6 +134,24 @@ int acr_residual(acr_handle h, const double* b, const double* x, double* r, int 
                  double* rel_norms);
 
 /*
+ * acr_residual_noalloc -- the same FP64 residual and relative norms as
+ * acr_residual, for callers that may not allocate device memory while they
+ * run (a memory budget reserved up front, or a loop that cannot absorb an
+ * allocation's implicit synchronisation).  The paper has no counterpart; this
+ * is a property of the library, not of the method.
+ *   Arguments as acr_residual; rel_norms is a host array of nrhs doubles or NULL.
+ *   nrhs must be 1..64: larger requests return ACR_ERR_ARG.
+ * The call allocates nothing: its reduction scratch is a fixed ~1 MiB array
+ * in device memory that every GPU using the library holds until the process
+ * exits.  The first call on each device looks up that array's device address
+ * (with the device current), so make the first call on a device before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ */
+int acr_residual_noalloc(acr_handle h, const double* b, const double* x, double* r, int nrhs, long ld,
+                         double* rel_norms);
+
+/*
  * acr_solve_ir -- ACR as preconditioner inside FP64 iterative refinement
  * (Section 5: low-accuracy factorisation plus an iterative procedure):
  * x_0 = 0; repeat d = M^{-1}(b - A x); x += d until every column has

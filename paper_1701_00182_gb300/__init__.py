@@ -96,6 +96,7 @@ def load_library():
         "acr_solve": (C.c_int, [H, P, P, C.c_int, C.c_long]),
         "acr_solve_transpose": (C.c_int, [H, P, P, C.c_int, C.c_long]),
         "acr_residual": (C.c_int, [H, P, P, P, C.c_int, C.c_long, C.POINTER(C.c_double)]),
+        "acr_residual_noalloc": (C.c_int, [H, P, P, P, C.c_int, C.c_long, C.POINTER(C.c_double)]),
         "acr_solve_ir": (C.c_int, [H, P, P, C.c_int, C.c_long, C.c_double, C.c_int, C.POINTER(C.c_int),
                                    C.POINTER(C.c_double)]),
         "acr_solve_fgmres": (C.c_int, [H, P, P, C.c_int, C.c_long, C.c_double, C.c_int, C.c_int,
@@ -232,6 +233,16 @@ def acr_residual(h: Handle, b, x, r) -> np.ndarray:
     p_r, _, _ = _cols(r, h.n)
     rel = (C.c_double * nrhs)()
     _check(load_library().acr_residual(h.ptr, p_b, p_x, p_r, nrhs, ld, rel), "acr_residual")
+    return np.array(rel[:])
+
+
+def acr_residual_noalloc(h: Handle, b, x, r) -> np.ndarray:
+    """acr_residual without any device allocation in the call (fixed scratch; nrhs <= 64)."""
+    p_b, nrhs, ld = _cols(b, h.n)
+    p_x, _, _ = _cols(x, h.n)
+    p_r, _, _ = _cols(r, h.n)
+    rel = (C.c_double * nrhs)()
+    _check(load_library().acr_residual_noalloc(h.ptr, p_b, p_x, p_r, nrhs, ld, rel), "acr_residual_noalloc")
     return np.array(rel[:])
 
 

@@ -444,6 +444,16 @@ void get_block_impl(acr_handle_s* h, FactorT<T>& f, int which, int level, int in
 
 }  // namespace
 
+namespace acr {
+int handle_residual_view(acr_handle h, cudaStream_t* st, int* n, const double** coef) {
+  if (!h || !h->coef.p) return ACR_ERR_ARG;
+  *st = h->ctx.st;
+  *n = h->n;
+  *coef = h->coef.p;
+  return ACR_OK;
+}
+}  // namespace acr
+
 extern "C" {
 
 void acr_default_opts(acr_opts* o) {

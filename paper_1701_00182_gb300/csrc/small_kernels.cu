@@ -468,6 +468,18 @@ void stencil_apply(Ctx& c, int n, int nrhs, const double* coef, const double* x,
   }
 }
 
+// Same kernels as stencil_apply with norms, but the per-block partial sums and
+// the per-column pairs live in caller-provided device scratch: part holds
+// nb_max * nrhs * 2 doubles, pairs 2 * nrhs.  Every entry read is written
+// earlier in the same call, so the scratch needs no clearing.  Allocates nothing.
+void stencil_norms_scratch(cudaStream_t st, int n, int nrhs, const double* coef, const double* x, long ld,
+                           const double* y, double* out, double* part, int nb_max, double* pairs) {
+  long N = (long)n * n * n;
+  int nb = (int)std::min<long>((N + 255) / 256, nb_max);
+  k_stencil<<<dim3(nb, nrhs), 256, 0, st>>>(n, nrhs, coef, x, ld, y, out, -1.0, 1.0, part);
+  k_reduce_pairs<<<nrhs, 256, 0, st>>>(nrhs, nb, part, pairs);
+}
+
 __global__ void k_col_dots(long N, const double* x, long ldx, const double* y, long ldy, double* part) {
   int col = blockIdx.y;
   __shared__ double s1[256];

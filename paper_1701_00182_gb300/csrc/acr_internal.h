@@ -106,6 +106,10 @@ template <class T>
 void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta,
           Op<T> C);
 
+// C = alpha * A B + beta * C for symmetric C (M x M, A = B^T): upper triangle computed, then mirrored.
+template <class T>
+void gemm_sym(Ctx& c, int M, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta, Op<T> C);
+
 // Panel view: rows m per plane, element (row, col) at p[plane*ps + row*ld + col].
 template <class T>
 struct Pan {

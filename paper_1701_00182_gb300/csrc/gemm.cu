@@ -22,6 +22,7 @@ struct GArgs {
   Op<T> A, B, C;
   int kchunk;
   T* partial;
+  int sym;  // C is symmetric (A = B^T): only tiles touching the upper triangle are computed
 };
 
 template <class T>
@@ -39,6 +40,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GArgs<T> g) {
   const int plane = bi / g.nclus, c = bi - plane * g.nclus;
   const int tilesN = (g.N + BN - 1) / BN;
   const int m0 = (blockIdx.y / tilesN) * BM, n0 = (blockIdx.y % tilesN) * BN;
+  if (g.sym && m0 >= n0 + BN) return;  // tile strictly below the diagonal
   const int kbeg = blockIdx.z * g.kchunk;
   const int kend = min(g.K, kbeg + g.kchunk);
   const T* __restrict__ A = opaddr(g.A, plane, c);
@@ -132,6 +134,7 @@ __global__ void k_splitk_reduce(GArgs<T> g, int nsplit) {
     long bi = e / ((long)g.M * g.N);
     long r = e - bi * (long)g.M * g.N;
     int i = (int)(r / g.N), j = (int)(r % g.N);
+    if (g.sym && i > j) continue;
     T s = T(0);
     for (int q = 0; q < nsplit; ++q) s += g.partial[((long)q * g.batch + bi) * (long)g.M * g.N + r];
     int plane = (int)(bi / g.nclus), c = (int)(bi - (long)plane * g.nclus);
@@ -139,6 +142,20 @@ __global__ void k_splitk_reduce(GArgs<T> g, int nsplit) {
     T v = g.alpha * s;
     if (g.beta != T(0)) v += g.beta * *cp;
     *cp = v;
+  }
+}
+
+template <class T>
+__global__ void k_mirror(GArgs<T> g) {
+  long tot = (long)g.batch * g.M * g.N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    long bi = e / ((long)g.M * g.N);
+    long r = e - bi * (long)g.M * g.N;
+    int i = (int)(r / g.N), j = (int)(r % g.N);
+    if (i <= j) continue;
+    int plane = (int)(bi / g.nclus), c = (int)(bi - (long)plane * g.nclus);
+    T* C = opaddr(g.C, plane, c);
+    C[(long)i * g.C.rs + (long)j * g.C.cs] = C[(long)j * g.C.rs + (long)i * g.C.cs];
   }
 }
 
@@ -212,7 +229,7 @@ static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch
     const double es = sizeof(T);
     c.kbegin();
     launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, split), g, c.st);
-    c.kend(KC_GEMM, 2.0 * M * N * K * batch, es * batch * ((double)M * K + (double)K * N + (double)M * N * split));
+    c.kend(KC_GEMM, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch, es * batch * ((double)M * K + (double)K * N + (double)M * N * split));
     long tot = batch * (long)M * N;
     int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
     c.kbegin();
@@ -224,7 +241,7 @@ static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch
     g.partial = nullptr;
     c.kbegin();
     launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, 1), g, c.st);
-    c.kend(KC_GEMM, 2.0 * M * N * K * batch,
+    c.kend(KC_GEMM, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch,
            (double)sizeof(T) * batch * ((double)M * K + (double)K * N + (double)M * N * (1 + (g.beta != T(0)))));
   }
 }
@@ -251,7 +268,8 @@ static void check_op(const Ctx& c, const Op<T>& o, int nplanes, int nclus, int r
 }
 
 template <class T>
-void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta, Op<T> C) {
+static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta, Op<T> C,
+                      int sym) {
   long batch = (long)nplanes * nclus;
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (c.check_bounds) {
@@ -263,7 +281,7 @@ void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A,
   }
   if (K <= 0) {
     // Empty inner dimension: C = beta * C.
-    GArgs<T> g{M, N, 0, nclus, (int)batch, T(0), beta, A, B, C, 0, nullptr};
+    GArgs<T> g{M, N, 0, nclus, (int)batch, T(0), beta, A, B, C, 0, nullptr, 0};
     long tot = batch * (long)M * N;
     int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
     c.kbegin();
@@ -272,8 +290,8 @@ void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A,
     return;
   }
   if (batch > 0x7fffffffL) throw AcrError(1, "gemm batch too large");
-  c.gemm_flops += 2LL * M * N * K * batch;
-  GArgs<T> g{M, N, K, nclus, (int)batch, alpha, beta, A, B, C, K, nullptr};
+  c.gemm_flops += (sym ? 1LL * M * (N + 1) : 2LL * M * N) * K * batch;
+  GArgs<T> g{M, N, K, nclus, (int)batch, alpha, beta, A, B, C, K, nullptr, sym};
   int cfg = heuristic_cfg(M, N, batch);
   int split = split_for(cfg, M, N, K, batch);
   if (c.autotune) {
@@ -321,8 +339,27 @@ void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A,
     split = (found >> 2) ? split_for(cfg, M, N, K, batch) : 1;
   }
   run_gemm<T>(c, cfg, split, M, N, K, batch, g);
+  if (sym) {
+    long tot = batch * (long)M * N;
+    int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
+    c.kbegin();
+    k_mirror<T><<<nb, 256, 0, c.st>>>(g);
+    c.kend(KC_COPY, 0, (double)sizeof(T) * tot);
+  }
 }
 
+template <class T>
+void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta, Op<T> C) {
+  gemm_impl<T>(c, M, N, K, nplanes, nclus, alpha, A, B, beta, C, 0);
+}
+
+template <class T>
+void gemm_sym(Ctx& c, int M, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta, Op<T> C) {
+  gemm_impl<T>(c, M, M, K, nplanes, nclus, alpha, A, B, beta, C, 1);
+}
+
+template void gemm_sym<float>(Ctx&, int, int, int, int, float, Op<float>, Op<float>, float, Op<float>);
+template void gemm_sym<double>(Ctx&, int, int, int, int, double, Op<double>, Op<double>, double, Op<double>);
 template void gemm<float>(Ctx&, int, int, int, int, int, float, Op<float>, Op<float>, float, Op<float>);
 template void gemm<double>(Ctx&, int, int, int, int, int, double, Op<double>, Op<double>, double,
                            Op<double>);

@@ -241,6 +241,53 @@ __global__ void __launch_bounds__(kCholThreads) k_pchol(int r, const T* Gall, T 
 // column (Hestenes), with a round-robin tournament so the ncol/2 disjoint
 // pairs of a step run on separate warps.  The working matrix lives in shared
 // memory when it fits (ldw = nrow), otherwise in the global work buffer.
+// One Hestenes rotation of columns (i, j) by one warp, the column segments
+// held in registers (lane owns rows lane + 32 q).  Returns true if rotated.
+template <class T, int RPT>
+__device__ __forceinline__ bool jacobi_pair(T* wi, T* wj, int nrow, T* vi, T* vj, int ncol, T eps, int lane) {
+  T x[RPT], y[RPT];
+  T a = 0, b = 0, g = 0;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    int idx = lane + 32 * q;
+    x[q] = idx < nrow ? wi[idx] : T(0);
+    y[q] = idx < nrow ? wj[idx] : T(0);
+    a += x[q] * x[q];
+    b += y[q] * y[q];
+    g += x[q] * y[q];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  g = warp_sum(g);
+  if (!(g != T(0) && fabs(g) > eps * sqrt(a * b))) return false;
+  T zeta = (b - a) / (T(2) * g);
+  T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+  T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    int idx = lane + 32 * q;
+    if (idx < nrow) {
+      wi[idx] = cs * x[q] - sn * y[q];
+      wj[idx] = sn * x[q] + cs * y[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    int idx = lane + 32 * q;
+    x[q] = idx < ncol ? vi[idx] : T(0);
+    y[q] = idx < ncol ? vj[idx] : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    int idx = lane + 32 * q;
+    if (idx < ncol) {
+      vi[idx] = cs * x[q] - sn * y[q];
+      vj[idx] = sn * x[q] + cs * y[q];
+    }
+  }
+  return true;
+}
+
 constexpr int kJacThreads = 1024;
 template <class T>
 __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, const int* kk, long NB, T* Wall, T* Vall,
@@ -298,34 +345,42 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
         if (i >= ncol || jx >= ncol) continue;
         T* wi = W + (long)i * ldw;
         T* wj = W + (long)jx * ldw;
-        T a = 0, b = 0, g = 0;
-        for (int q = lane; q < nrow; q += 32) {
-          T x = wi[q], y = wj[q];
-          a += x * x;
-          b += y * y;
-          g += x * y;
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
-        if (g != T(0) && fabs(g) > eps * sqrt(a * b)) {
-          T zeta = (b - a) / (T(2) * g);
-          T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+        T* vi = V + (long)i * r;
+        T* vj = V + (long)jx * r;
+        bool rotd;
+        if (nrow <= 256) rotd = jacobi_pair<T, 8>(wi, wj, nrow, vi, vj, ncol, eps, lane);
+        else if (sizeof(T) == 4 && nrow <= 512)
+          rotd = jacobi_pair<T, (sizeof(T) == 4 ? 16 : 8)>(wi, wj, nrow, vi, vj, ncol, eps, lane);
+        else {
+          rotd = false;
+          T a = 0, b = 0, g = 0;
           for (int q = lane; q < nrow; q += 32) {
             T x = wi[q], y = wj[q];
-            wi[q] = cs * x - sn * y;
-            wj[q] = sn * x + cs * y;
+            a += x * x;
+            b += y * y;
+            g += x * y;
           }
-          T* vi = V + (long)i * r;
-          T* vj = V + (long)jx * r;
-          for (int q = lane; q < ncol; q += 32) {
-            T x = vi[q], y = vj[q];
-            vi[q] = cs * x - sn * y;
-            vj[q] = sn * x + cs * y;
+          a = warp_sum(a);
+          b = warp_sum(b);
+          g = warp_sum(g);
+          if (g != T(0) && fabs(g) > eps * sqrt(a * b)) {
+            T zeta = (b - a) / (T(2) * g);
+            T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+            T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+            for (int q = lane; q < nrow; q += 32) {
+              T x = wi[q], y = wj[q];
+              wi[q] = cs * x - sn * y;
+              wj[q] = sn * x + cs * y;
+            }
+            for (int q = lane; q < ncol; q += 32) {
+              T x = vi[q], y = vj[q];
+              vi[q] = cs * x - sn * y;
+              vj[q] = sn * x + cs * y;
+            }
+            rotd = true;
           }
-          if (lane == 0) s_rot = 1;
         }
+        if (rotd && lane == 0) s_rot = 1;
       }
       __syncthreads();
     }
@@ -460,7 +515,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
       Op<T> B{F, r, 1, (long)m * r, (long)s * r, 0, 0, side};
       Op<T> C{G.p + side * NB * r * (long)r, r, 1, (long)nclus * r * r, (long)r * r, 0, 0, 0};
       c.tag = "gram";
-      gemm<T>(c, r, r, s, P, nclus, T(1), A, B, T(0), C);
+      gemm_sym<T>(c, r, s, P, nclus, T(1), A, B, T(0), C);
     }
     scale = DBuf<T>(c, 2 * NB * (size_t)r);
     c.kbegin();

@@ -64,6 +64,7 @@ typedef struct {
   int nrhs_max;           /* solve workspace is sized for this many right-hand sides (default 64) */
   void* cuda_stream;      /* cudaStream_t to run on; NULL = legacy default stream */
   int profile;            /* 1 = time every kernel launch with CUDA events (per-class totals in acr_stats) */
+  int inverse_fp64;       /* ACR_FP32 only: 1 = leaf and Woodbury-coupling inverses computed in FP64 */
 } acr_opts;
 
 typedef struct {

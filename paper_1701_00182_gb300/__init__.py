@@ -44,6 +44,7 @@ class AcrOpts(C.Structure):
         ("nrhs_max", C.c_int),
         ("cuda_stream", C.c_void_p),
         ("profile", C.c_int),
+        ("inverse_fp64", C.c_int),
     ]
 
 

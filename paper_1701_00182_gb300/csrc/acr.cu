@@ -510,6 +510,7 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     c.check_bounds = cb && cb[0] == '1';
     c.autotune = o.autotune != 0;
     c.profile = o.profile != 0;
+    c.inverse_fp64 = o.inverse_fp64 != 0;
     ACR_CUDA(cudaMalloc(&c.d_flag, 4 * sizeof(int)));
     ACR_CUDA(cudaMemsetAsync(c.d_flag, 0, 4 * sizeof(int), c.st));
     h->n = n;

@@ -53,7 +53,8 @@ struct Ctx {
   bool autotune = false;
   std::vector<std::pair<unsigned long long, int>> tuned;  // shape key -> config
   std::map<uintptr_t, size_t> live;  // allocation start -> bytes (for the operand extent check)
-  bool check_bounds = false;         // ACR_CHECK_BOUNDS=1: verify every GEMM operand range on the host
+  bool check_bounds = false;
+  bool inverse_fp64 = false;         // FP32 factorisation: leaf and coupling inverses in FP64         // ACR_CHECK_BOUNDS=1: verify every GEMM operand range on the host
   void check_range(const void* base, long lo, long hi, size_t es, const char* what) const;
   bool profile = false;  // record CUDA events around every launch, accumulated per kernel class
   double kc_ms[16] = {}, kc_flops[16] = {}, kc_bytes[16] = {};

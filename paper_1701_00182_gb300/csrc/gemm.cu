@@ -127,6 +127,119 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GArgs<T> g) {
   }
 }
 
+// FP32 128 x 128 tile, BK = 8, 256 threads, 8 x 8 outputs per thread arranged
+// as four 4 x 4 quadrants (rows ty*4 + {0, 64}, columns tx*4 + {0, 64}) so the
+// shared-memory reads are float4 and bank-conflict free.  The next K tile is
+// fetched into registers while the current one is consumed (double buffer).
+__global__ void __launch_bounds__(256) k_gemm_f32_big(GArgs<float> g) {
+  constexpr int BM = 128, BN = 128, BK = 8;
+  __shared__ __align__(16) float As[2][BK][BM];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+  const int bi = blockIdx.x;
+  const int plane = bi / g.nclus, c = bi - plane * g.nclus;
+  const int tilesN = (g.N + BN - 1) / BN;
+  const int m0 = (blockIdx.y / tilesN) * BM, n0 = (blockIdx.y % tilesN) * BN;
+  if (g.sym && m0 >= n0 + BN) return;
+  const int kbeg = blockIdx.z * g.kchunk;
+  const int kend = min(g.K, kbeg + g.kchunk);
+  const float* __restrict__ A = opaddr(g.A, plane, c);
+  const float* __restrict__ B = opaddr(g.B, plane, c);
+  const long ars = g.A.rs, acs = g.A.cs, brs = g.B.rs, bcs = g.B.cs;
+  const bool a_kfast = (acs == 1), b_nfast = (bcs == 1);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // Each thread stages 4 elements of the A tile and 4 of the B tile.
+  float ra[4], rb[4];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int e = tid + 256 * u;
+      int ii, kk;
+      if (a_kfast) { ii = e >> 3; kk = e & 7; } else { ii = e & 127; kk = e >> 7; }
+      int gi = m0 + ii, gk = k0 + kk;
+      ra[u] = (gi < g.M && gk < kend) ? A[(long)gi * ars + (long)gk * acs] : 0.f;
+      int jj, kb;
+      if (b_nfast) { jj = e & 127; kb = e >> 7; } else { jj = e >> 3; kb = e & 7; }
+      int gj = n0 + jj, gk2 = k0 + kb;
+      rb[u] = (gk2 < kend && gj < g.N) ? B[(long)gk2 * brs + (long)gj * bcs] : 0.f;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int e = tid + 256 * u;
+      int ii, kk;
+      if (a_kfast) { ii = e >> 3; kk = e & 7; } else { ii = e & 127; kk = e >> 7; }
+      As[buf][kk][ii] = ra[u];
+      int jj, kb;
+      if (b_nfast) { jj = e & 127; kb = e >> 7; } else { jj = e >> 3; kb = e & 7; }
+      Bs[buf][kb][jj] = rb[u];
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  int buf = 0;
+  if (kbeg < kend) {
+    fetch(kbeg);
+    stash(0);
+  }
+  __syncthreads();
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool more = k0 + BK < kend;
+    if (more) fetch(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4 + 64]);
+      float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4 + 64]);
+      float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  auto row_of = [&](int i) { return m0 + ty * 4 + (i & 3) + ((i >> 2) << 6); };
+  auto col_of = [&](int j) { return n0 + tx * 4 + (j & 3) + ((j >> 2) << 6); };
+  if (g.partial) {
+    float* P = g.partial + ((long)blockIdx.z * g.batch + bi) * (long)g.M * g.N;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      int gi = row_of(i);
+      if (gi >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        int gj = col_of(j);
+        if (gj < g.N) P[(long)gi * g.N + gj] = acc[i][j];
+      }
+    }
+    return;
+  }
+  float* C = opaddr(g.C, plane, c);
+  const long crs = g.C.rs, ccs = g.C.cs;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int gi = row_of(i);
+    if (gi >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      int gj = col_of(j);
+      if (gj >= g.N) continue;
+      float* cp = C + (long)gi * crs + (long)gj * ccs;
+      float v = g.alpha * acc[i][j];
+      if (g.beta != 0.f) v += g.beta * *cp;
+      *cp = v;
+    }
+  }
+}
+
 template <class T>
 __global__ void k_splitk_reduce(GArgs<T> g, int nsplit) {
   long tot = (long)g.batch * g.M * g.N;
@@ -177,7 +290,7 @@ namespace {
 struct Cfg {
   int bm, bn, bk;
 };
-constexpr Cfg kCfg[4] = {{64, 64, 16}, {128, 64, 8}, {32, 32, 32}, {128, 128, 8}};
+constexpr Cfg kCfg[5] = {{64, 64, 16}, {128, 64, 8}, {32, 32, 32}, {128, 128, 8}, {128, 128, 8}};
 
 template <class T>
 void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st) {
@@ -185,13 +298,17 @@ void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st) {
     case 0: k_gemm<T, 64, 64, 16, 4, 4><<<grid, 256, 0, st>>>(g); break;
     case 1: k_gemm<T, 128, 64, 8, 8, 4><<<grid, 256, 0, st>>>(g); break;
     case 2: k_gemm<T, 32, 32, 32, 2, 2><<<grid, 256, 0, st>>>(g); break;
-    default: k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g); break;
+    case 3: k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g); break;
+    default:
+      if constexpr (sizeof(T) == 4) k_gemm_f32_big<<<grid, 256, 0, st>>>(g);
+      else k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g);
+      break;
   }
 }
 
-int heuristic_cfg(int M, int N, long batch) {
+int heuristic_cfg(int M, int N, long batch, int es) {
   if (M <= 32 && N <= 32) return 2;
-  if (M >= 128 && N >= 128 && batch * ((M + 127) / 128) * ((N + 127) / 128) >= 2 * 152) return 3;
+  if (M >= 96 && N >= 96) return es == 4 ? 4 : 3;
   if (M >= 128 && N <= 64) return 1;
   return 0;
 }
@@ -292,7 +409,7 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
   if (batch > 0x7fffffffL) throw AcrError(1, "gemm batch too large");
   c.gemm_flops += (sym ? 1LL * M * (N + 1) : 2LL * M * N) * K * batch;
   GArgs<T> g{M, N, K, nclus, (int)batch, alpha, beta, A, B, C, K, nullptr, sym};
-  int cfg = heuristic_cfg(M, N, batch);
+  int cfg = heuristic_cfg(M, N, batch, (int)sizeof(T));
   int split = split_for(cfg, M, N, K, batch);
   if (c.autotune) {
     unsigned long long key = shape_key(sizeof(T), M, N, K, batch);
@@ -315,10 +432,10 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
       ACR_CUDA(cudaEventCreate(&e1));
       float best = 1e30f;
       int bestc = 0;
-      for (int cand = 0; cand < 8; ++cand) {
-        int cf = cand & 3;
-        int sp = (cand >> 2) ? split_for(cf, M, N, K, batch) : 1;
-        if ((cand >> 2) && sp == 1) continue;
+      for (int cand = 0; cand < 10; ++cand) {
+        int cf = cand % 5;
+        int sp = (cand / 5) ? split_for(cf, M, N, K, batch) : 1;
+        if ((cand / 5) && sp == 1) continue;
         run_gemm<T>(c, cf, sp, M, N, K, batch, gt);  // warm
         ACR_CUDA(cudaEventRecord(e0, c.st));
         run_gemm<T>(c, cf, sp, M, N, K, batch, gt);
@@ -335,8 +452,8 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tuned.push_back({key, found});
     }
-    cfg = found & 3;
-    split = (found >> 2) ? split_for(cfg, M, N, K, batch) : 1;
+    cfg = found % 5;
+    split = (found / 5) ? split_for(cfg, M, N, K, batch) : 1;
   }
   run_gemm<T>(c, cfg, split, M, N, K, batch, g);
   if (sym) {

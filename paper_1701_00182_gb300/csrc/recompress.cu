@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(kCholThreads) k_pchol(int r, const T* Gall, T 
 // One Hestenes rotation of columns (i, j) by one warp, the column segments
 // held in registers (lane owns rows lane + 32 q).  Returns true if rotated.
 template <class T, int RPT>
-__device__ __forceinline__ bool jacobi_pair(T* wi, T* wj, int nrow, T* vi, T* vj, int ncol, T eps, int lane) {
+__device__ __forceinline__ bool jacobi_pair(T* wi, T* wj, int nrow, T* vi, T* vj, int ncol, T eps, T floor2,
+                                            int lane) {
   T x[RPT], y[RPT];
   T a = 0, b = 0, g = 0;
 #pragma unroll
@@ -259,6 +260,7 @@ __device__ __forceinline__ bool jacobi_pair(T* wi, T* wj, int nrow, T* vi, T* vj
   a = warp_sum(a);
   b = warp_sum(b);
   g = warp_sum(g);
+  if (fmin(a, b) <= floor2) return false;  // a negligible column: its rotation cannot matter
   if (!(g != T(0) && fabs(g) > eps * sqrt(a * b))) return false;
   T zeta = (b - a) / (T(2) * g);
   T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
@@ -327,7 +329,25 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
     int row = (int)(e % ncol), col = (int)(e / ncol);
     V[(long)col * r + row] = (row == col) ? T(1) : T(0);
   }
+  __shared__ T s_fro[32];
+  {
+    T part = T(0);
+    for (long e = tid; e < (long)nrow * ncol; e += blockDim.x) {
+      int row = (int)(e % nrow), col = (int)(e / nrow);
+      T v = W[(long)col * ldw + row];
+      part += v * v;
+    }
+    part = warp_sum(part);
+    if (lane == 0) s_fro[warp] = part;
+  }
   __syncthreads();
+  T fro2 = T(0);
+  for (int w = 0; w < nw; ++w) fro2 += s_fro[w];
+  // Columns whose squared norm is below tau ||C||_F^2 lie far below the
+  // truncation threshold; Jacobi leaves them alone (their pairwise cosines
+  // are rounding noise and would never settle).
+  const T tau = fmax(T(1e-4) * tol * tol, T(16) * unit * unit);
+  const T floor2 = tau * fro2;
   const int ne = ncol + (ncol & 1);
   for (int sw = 0; sw < maxsweeps && ne > 1; ++sw) {
     if (tid == 0) s_rot = 0;
@@ -348,9 +368,9 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
         T* vi = V + (long)i * r;
         T* vj = V + (long)jx * r;
         bool rotd;
-        if (nrow <= 256) rotd = jacobi_pair<T, 8>(wi, wj, nrow, vi, vj, ncol, eps, lane);
+        if (nrow <= 256) rotd = jacobi_pair<T, 8>(wi, wj, nrow, vi, vj, ncol, eps, floor2, lane);
         else if (sizeof(T) == 4 && nrow <= 512)
-          rotd = jacobi_pair<T, (sizeof(T) == 4 ? 16 : 8)>(wi, wj, nrow, vi, vj, ncol, eps, lane);
+          rotd = jacobi_pair<T, (sizeof(T) == 4 ? 16 : 8)>(wi, wj, nrow, vi, vj, ncol, eps, floor2, lane);
         else {
           rotd = false;
           T a = 0, b = 0, g = 0;
@@ -363,7 +383,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
           a = warp_sum(a);
           b = warp_sum(b);
           g = warp_sum(g);
-          if (g != T(0) && fabs(g) > eps * sqrt(a * b)) {
+          if (fmin(a, b) > floor2 && g != T(0) && fabs(g) > eps * sqrt(a * b)) {
             T zeta = (b - a) / (T(2) * g);
             T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
             T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;

@@ -175,9 +175,28 @@ __global__ void __launch_bounds__(kGJThreads) k_gj_inverse(int n, T* A, long str
   }
 }
 
+template <class S, class D>
+__global__ void k_convert(long n, const S* a, D* b) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) b[i] = D(a[i]);
+}
+
 template <class T>
 int batched_inverse(Ctx& c, int nb, int n, T* A, long stride) {
   if (nb <= 0 || n <= 0) return 0;
+  if (sizeof(T) == 4 && c.inverse_fp64 && stride == (long)n * n) {
+    // Small inverses of the FP32 factorisation carried out in FP64.
+    long tot = (long)nb * n * n;
+    double* Ad = c.alloc<double>(tot);
+    c.kbegin();
+    k_convert<T, double><<<nblk(tot), 256, 0, c.st>>>(tot, A, Ad);
+    c.kend(KC_COPY, 0, 12.0 * tot);
+    batched_inverse<double>(c, nb, n, Ad, stride);
+    c.kbegin();
+    k_convert<double, T><<<nblk(tot), 256, 0, c.st>>>(tot, Ad, A);
+    c.kend(KC_COPY, 0, 12.0 * tot);
+    c.free(Ad, tot);
+    return 0;
+  }
   size_t sm = 2 * (size_t)n * sizeof(T) + (size_t)n * sizeof(int);
   if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_gj_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   if (sm > 200 * 1024) throw AcrError(4, "coupling matrix too large");

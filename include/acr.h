@@ -65,6 +65,8 @@ typedef struct {
   void* cuda_stream;      /* cudaStream_t to run on; NULL = legacy default stream */
   int profile;            /* 1 = time every kernel launch with CUDA events (per-class totals in acr_stats) */
   int inverse_fp64;       /* ACR_FP32 only: 1 = leaf and Woodbury-coupling inverses computed in FP64 */
+  int graphs;             /* 1 = capture the solve sweeps once per (nrhs, transpose) as a CUDA graph and replay
+                             it; with cuda_stream NULL the handle then runs on its own blocking stream */
 } acr_opts;
 
 typedef struct {
@@ -88,6 +90,7 @@ typedef struct {
   double kc_bytes[16];
   long long kc_launches[16];
   int jacobi_sweeps_max;                  /* most Jacobi sweeps any core SVD of the factorisation needed */
+  int graphs_captured;                    /* solve graphs captured so far */
 } acr_stats;
 
 /* Default options (FP64, shift 0, unlimited ranks and memory, autotune off, nrhs_max 64). */

@@ -45,6 +45,7 @@ class AcrOpts(C.Structure):
         ("cuda_stream", C.c_void_p),
         ("profile", C.c_int),
         ("inverse_fp64", C.c_int),
+        ("graphs", C.c_int),
     ]
 
 
@@ -69,6 +70,7 @@ class AcrStats(C.Structure):
         ("kc_bytes", C.c_double * 16),
         ("kc_launches", C.c_longlong * 16),
         ("jacobi_sweeps_max", C.c_int),
+        ("graphs_captured", C.c_int),
     ]
 
 
@@ -292,6 +294,7 @@ def acr_get_stats(h: Handle) -> dict:
         "t_level_ms": [s.t_level_ms[r] for r in range(min(q, 16))], "gemm_flops": s.gemm_flops,
         "kernel_launches": s.kernel_launches,
         "jacobi_sweeps_max": s.jacobi_sweeps_max,
+        "graphs_captured": s.graphs_captured,
         "kernels": {nm: {"ms": s.kc_ms[i], "flops": s.kc_flops[i], "bytes": s.kc_bytes[i],
                          "launches": s.kc_launches[i]} for i, nm in enumerate(KERNEL_CLASSES)},
     }

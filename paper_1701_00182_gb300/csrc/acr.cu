@@ -134,6 +134,10 @@ struct FactorT {
   HStore<T> Xc;
   DBuf<T> Fint, tmp;
   int cap = 0;
+  std::vector<std::pair<long, cudaGraphExec_t>> graphs;  // key nrhs*2 + transpose
+  ~FactorT() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+  }
 };
 
 }  // namespace acr
@@ -143,6 +147,8 @@ using namespace acr;
 struct acr_handle_s {
   Ctx ctx;
   int n = 0, leaf = 0, precision = ACR_FP64, nrhs_max = 64, max_rank = 0;
+  bool graphs = false;
+  cudaStream_t own_stream = nullptr;
   double tol = 0, shift = 0;
   Geometry geo;
   DBuf<int> perm, iperm;
@@ -162,6 +168,7 @@ struct acr_handle_s {
     coef.release();
     if (ctx.d_flag) cudaFree(ctx.d_flag);
     if (ctx.st) cudaStreamSynchronize(ctx.st);
+    if (own_stream) cudaStreamDestroy(own_stream);
     const char* ps = std::getenv("ACR_PROFILE_SITES");
     if (ps && ps[0] == '1' && !ctx.site.empty()) {
       ctx.kflush();
@@ -322,22 +329,12 @@ long factor_bytes(const FactorT<T>& f) {
   return s;
 }
 
-// x = M^{-1} rhs (or M^{-T}); accumulate adds into x.
+// The forward-reduction / coarsest / back-substitution sweeps on the
+// internal RHS buffer F (n planes of m x nrhs), M^{-1} or M^{-T}.
 template <class T>
-void solve_impl(acr_handle_s* h, FactorT<T>& fac, const double* rhs, double* x, int nrhs, long ld, bool trans,
-                bool accumulate) {
+void sweeps(acr_handle_s* h, FactorT<T>& fac, T* Fint, T* tmp, int nrhs, bool trans) {
   Ctx& c = h->ctx;
   const int n = h->geo.n, m = h->geo.m, q = fac.q;
-  DBuf<T> Fown, Town;
-  T* Fint = fac.Fint.p;
-  T* tmp = fac.tmp.p;
-  if (nrhs > fac.cap) {
-    Fown = DBuf<T>(c, (size_t)n * m * nrhs);
-    Town = DBuf<T>(c, (size_t)std::max(1, n / 2) * m * nrhs);
-    Fint = Fown.p;
-    tmp = Town.p;
-  }
-  permute_in<T>(c, n, nrhs, rhs, ld, h->perm.p, Fint);
   const long pst = (long)m * nrhs;
   auto view = [&](int r, int pos0) {
     long step = 1L << r;
@@ -380,6 +377,61 @@ void solve_impl(acr_handle_s* h, FactorT<T>& fac, const double* rhs, double* x, 
       hmatvec<T>(c, lv.G.h, 0, true, view(r, 1), view(r, 0), nrhs, T(-1), T(1));
       if (ne > 1) hmatvec<T>(c, lv.H.h, 0, true, view(r, 1), view(r, 2), nrhs, T(-1), T(1));
     }
+  }
+}
+
+// x = M^{-1} rhs (or M^{-T}); accumulate adds into x.  With graphs enabled the
+// sweeps for a given (nrhs, transpose) are captured once and replayed.
+template <class T>
+void solve_impl(acr_handle_s* h, FactorT<T>& fac, const double* rhs, double* x, int nrhs, long ld, bool trans,
+                bool accumulate) {
+  Ctx& c = h->ctx;
+  const int n = h->geo.n, m = h->geo.m;
+  DBuf<T> Fown, Town;
+  T* Fint = fac.Fint.p;
+  T* tmp = fac.tmp.p;
+  const bool own = nrhs > fac.cap;
+  if (own) {
+    Fown = DBuf<T>(c, (size_t)n * m * nrhs);
+    Town = DBuf<T>(c, (size_t)std::max(1, n / 2) * m * nrhs);
+    Fint = Fown.p;
+    tmp = Town.p;
+  }
+  permute_in<T>(c, n, nrhs, rhs, ld, h->perm.p, Fint);
+  if (h->graphs && !own && c.st) {
+    const long key = 2L * nrhs + (trans ? 1 : 0);
+    cudaGraphExec_t ex = nullptr;
+    for (auto& g : fac.graphs)
+      if (g.first == key) ex = g.second;
+    if (!ex) {
+      const bool prof = c.profile, tune = c.autotune, chk = c.check_bounds;
+      c.profile = false;  // no event timing or host synchronisation inside a capture
+      c.autotune = false;
+      cudaGraph_t graph = nullptr;
+      ACR_CUDA(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
+      try {
+        sweeps<T>(h, fac, Fint, tmp, nrhs, trans);
+      } catch (...) {
+        cudaStreamEndCapture(c.st, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        c.profile = prof;
+        c.autotune = tune;
+        throw;
+      }
+      ACR_CUDA(cudaStreamEndCapture(c.st, &graph));
+      c.profile = prof;
+      c.autotune = tune;
+      c.check_bounds = chk;
+      cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+      cudaGraphDestroy(graph);
+      ACR_CUDA(e);
+      fac.graphs.push_back({key, ex});
+      h->stats.graphs_captured++;
+    }
+    ACR_CUDA(cudaGraphLaunch(ex, c.st));
+    c.launches += 1;
+  } else {
+    sweeps<T>(h, fac, Fint, tmp, nrhs, trans);
   }
   permute_out<T>(c, n, nrhs, Fint, h->perm.p, x, ld, accumulate ? 1 : 0);
 }
@@ -505,6 +557,13 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     }
     Ctx& c = h->ctx;
     c.st = (cudaStream_t)o.cuda_stream;
+    h->graphs = o.graphs != 0;
+    if (h->graphs && !c.st) {
+      // The legacy default stream cannot be captured: run on a private blocking
+      // stream (it still orders with the legacy default stream).
+      ACR_CUDA(cudaStreamCreate(&h->own_stream));
+      c.st = h->own_stream;
+    }
     c.budget = o.mem_budget;
     const char* cb = std::getenv("ACR_CHECK_BOUNDS");
     c.check_bounds = cb && cb[0] == '1';

@@ -164,3 +164,29 @@ def test_stats_report_exact_level0_ranks(acr):
     assert s["max_rank_d"][0] == [16, 8, 8]
     assert s["factor_bytes"] > 0 and s["t_factor_ms"] > 0
     assert all(0 <= k <= 128 for row in s["max_rank"] for k in row)
+
+
+def test_solve_graphs_replay_bit_identical(acr):
+    """Captured solve sweeps (one CUDA graph per nrhs / transpose) give the
+    same bits as the eager launches, on repeated and refined solves."""
+    n = 16
+    g = synthetic.gaussian_random_field(n, 6)
+    F = synthetic.multi_rhs(n, [1, 2, 3])
+    he = acr.acr_factor(n, g, 1e-6, 32, precision=acr.ACR_FP32)
+    hg = acr.acr_factor(n, g, 1e-6, 32, precision=acr.ACR_FP32, graphs=1)
+    for cols in ([0], [0, 1, 2], [0]):
+        b = to_cols(F[:, cols])
+        xe, xg = empty_like_cols(b), empty_like_cols(b)
+        acr.acr_solve(he, b, xe)
+        acr.acr_solve(hg, b, xg)
+        np.testing.assert_array_equal(from_cols(xg), from_cols(xe))
+        acr.acr_solve_transpose(he, b, xe)
+        acr.acr_solve_transpose(hg, b, xg)
+        np.testing.assert_array_equal(from_cols(xg), from_cols(xe))
+    assert acr.acr_get_stats(hg)["graphs_captured"] == 4
+    b = to_cols(F)
+    xe, xg = empty_like_cols(b), empty_like_cols(b)
+    ite, rele, _ = acr.acr_solve_ir(he, b, xe, rtol=1e-10)
+    itg, relg, _ = acr.acr_solve_ir(hg, b, xg, rtol=1e-10)
+    assert ite == itg and max(relg) <= 1e-10
+    np.testing.assert_array_equal(from_cols(xg), from_cols(xe))

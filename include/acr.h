@@ -169,6 +169,24 @@ int acr_solve_ir(acr_handle h, const double* b, double* x, int nrhs, long ld, do
                  int* iters, double* rel_res);
 
 /*
+ * acr_solve_ir_transpose -- refinement with the transpose solve:
+ * x_0 = 0; repeat x += M^{-T}(b - A^T x).  The residual uses the 7-point
+ * operator, which is symmetric, so A^T x = A x.  Arguments as acr_solve_ir.
+ */
+int acr_solve_ir_transpose(acr_handle h, const double* b, double* x, int nrhs, long ld, double rtol, int maxit,
+                           int* iters, double* rel_res);
+
+/*
+ * acr_grad_logkappa -- adjoint coefficient gradient (the paper has no
+ * adjoint; derived from the operator of Section 2.2.1):
+ *   grad_p = - kappa_p sum_columns lambda^T (dA/dkappa_p) u
+ * for the handle's kappa, i.e. dL/dlog(kappa_p) when lambda = A^{-T} dL/du.
+ * u, lam: device FP64, N x nrhs, leading dimension ld; grad: device FP64,
+ * N entries (overwritten; contributions of all columns are summed).
+ */
+int acr_grad_logkappa(acr_handle h, const double* u, const double* lam, double* grad, int nrhs, long ld);
+
+/*
  * acr_solve_fgmres -- right-preconditioned flexible GMRES(restart) in FP64
  * with the ACR solve as preconditioner and modified Gram-Schmidt, run for
  * every column independently (all columns advance together).  For the

@@ -102,6 +102,9 @@ def load_library():
         "acr_residual_noalloc": (C.c_int, [H, P, P, P, C.c_int, C.c_long, C.POINTER(C.c_double)]),
         "acr_solve_ir": (C.c_int, [H, P, P, C.c_int, C.c_long, C.c_double, C.c_int, C.POINTER(C.c_int),
                                    C.POINTER(C.c_double)]),
+        "acr_solve_ir_transpose": (C.c_int, [H, P, P, C.c_int, C.c_long, C.c_double, C.c_int, C.POINTER(C.c_int),
+                                             C.POINTER(C.c_double)]),
+        "acr_grad_logkappa": (C.c_int, [H, P, P, P, C.c_int, C.c_long]),
         "acr_solve_fgmres": (C.c_int, [H, P, P, C.c_int, C.c_long, C.c_double, C.c_int, C.c_int,
                                        C.POINTER(C.c_int), C.POINTER(C.c_double)]),
         "acr_get_factor_block": (C.c_int, [H, C.c_int, C.c_int, C.c_int, P]),
@@ -261,6 +264,28 @@ def acr_solve_ir(h: Handle, b, x, rtol: float = 1e-10, maxit: int = 50, check: b
     return it.value, np.array(rel[:]), st
 
 
+def acr_solve_ir_transpose(h: Handle, b, x, rtol: float = 1e-10, maxit: int = 50, check: bool = True):
+    """Refinement with the transpose solve; returns (iterations, relative residuals, status)."""
+    p_b, nrhs, ld = _cols(b, h.n)
+    p_x, _, _ = _cols(x, h.n)
+    it = C.c_int(0)
+    rel = (C.c_double * nrhs)()
+    st = load_library().acr_solve_ir_transpose(h.ptr, p_b, p_x, nrhs, ld, float(rtol), int(maxit), C.byref(it), rel)
+    if check:
+        _check(st, "acr_solve_ir_transpose")
+    return it.value, np.array(rel[:]), st
+
+
+def acr_grad_logkappa(h: Handle, u, lam, grad) -> None:
+    """grad (float64 CUDA, N) = -kappa * sum_columns lam^T (dA/dkappa) u."""
+    p_u, nrhs, ld = _cols(u, h.n)
+    p_l, nrhs2, ld2 = _cols(lam, h.n)
+    if nrhs != nrhs2 or ld != ld2:
+        raise ValueError("u and lam must have the same shape and leading dimension")
+    p_g, _, _ = _cols(grad, h.n)
+    _check(load_library().acr_grad_logkappa(h.ptr, p_u, p_l, p_g, nrhs, ld), "acr_grad_logkappa")
+
+
 def acr_solve_fgmres(h: Handle, b, x, rtol: float = 1e-10, restart: int = 50, maxit: int = 500, check: bool = True):
     """FP64 right-preconditioned FGMRES with ACR; returns (preconditioner applications, rel. residuals, status)."""
     p_b, nrhs, ld = _cols(b, h.n)
@@ -316,3 +341,64 @@ def acr_plane_ordering(n: int, leaf: int):
     if L < 0:
         raise AcrError(-L, "acr_plane_ordering")
     return perm, ncut[:L].copy()
+
+
+def _colmajor(t):
+    """Same values as an (N,) / (N, r) column-major CUDA tensor."""
+    if t.dim() == 1:
+        return t.contiguous()
+    return t.t().contiguous().t()
+
+
+def _autograd_function():
+    import torch
+
+    class ACRSolve(torch.autograd.Function):
+        """u = A(exp(log_kappa))^{-1} f through ACR; backward by the transpose solve.
+
+        forward: acr_factor + acr_solve (or refinement to rtol); backward:
+        lambda = A^{-T} grad_u (acr_solve_transpose, or transpose refinement),
+        grad_f = lambda, grad_log_kappa = acr_grad_logkappa(u, lambda).  The
+        factorisation of the forward pass is kept for the backward pass.
+        """
+
+        @staticmethod
+        def forward(ctx, log_kappa, f, n, tol, leaf, precision, rtol):
+            h = acr_factor(n, log_kappa.detach().contiguous(), tol, leaf, precision=precision,
+                           nrhs_max=1 if f.dim() == 1 else f.shape[1])
+            fb = _colmajor(f.detach())
+            x = _colmajor(torch.zeros_like(fb))
+            if rtol:
+                acr_solve_ir(h, fb, x, rtol=rtol, maxit=80)
+            else:
+                acr_solve(h, fb, x)
+            ctx.h, ctx.rtol, ctx.n = h, rtol, n
+            ctx.save_for_backward(x)
+            return x
+
+        @staticmethod
+        def backward(ctx, gu):
+            (u,) = ctx.saved_tensors
+            h = ctx.h
+            g = _colmajor(gu.detach())
+            lam = _colmajor(torch.zeros_like(g))
+            if ctx.rtol:
+                acr_solve_ir_transpose(h, g, lam, rtol=ctx.rtol, maxit=80)
+            else:
+                acr_solve_transpose(h, g, lam)
+            grad = torch.zeros(ctx.n ** 3, dtype=torch.float64, device=u.device)
+            acr_grad_logkappa(h, u, lam, grad)
+            return grad, lam, None, None, None, None, None
+
+    return ACRSolve
+
+
+_ACRSolve = None
+
+
+def acr_solve_autograd(log_kappa, f, n: int, tol: float, leaf: int, precision: int = ACR_FP64, rtol=None):
+    """Differentiable solve u(log_kappa, f) on CUDA float64 tensors (see ACRSolve)."""
+    global _ACRSolve
+    if _ACRSolve is None:
+        _ACRSolve = _autograd_function()
+    return _ACRSolve.apply(log_kappa, f, n, tol, leaf, precision, rtol)

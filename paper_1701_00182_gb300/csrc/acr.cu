@@ -496,6 +496,45 @@ void get_block_impl(acr_handle_s* h, FactorT<T>& f, int which, int level, int in
 
 }  // namespace
 
+int solve_ir_impl(acr_handle h, const double* b, double* x, int nrhs, long ld, double rtol, int maxit,
+                         int* iters, double* rel_res, bool trans) {
+  if (!h || !b || !x || nrhs < 1 || maxit < 1 || ld < (long)h->n * h->n * h->n || b == x) return ACR_ERR_ARG;
+  bool conv = false;
+  int it = 0;
+  int st = guard([&] {
+    Ctx& c = h->ctx;
+    h->ctx.launches = 0;
+    const long N = (long)h->n * h->n * h->n;
+    DBuf<double> r(c, (size_t)ld * nrhs), nrm(c, 2 * (size_t)nrhs);
+    ACR_CUDA(cudaMemset2DAsync(x, ld * sizeof(double), 0, N * sizeof(double), nrhs, c.st));
+    ACR_CUDA(cudaMemcpy2DAsync(r.p, ld * sizeof(double), b, ld * sizeof(double), N * sizeof(double), nrhs,
+                               cudaMemcpyDeviceToDevice, c.st));
+    std::vector<double> hn(2 * nrhs), rel(nrhs, 1.0);
+    for (it = 1; it <= maxit; ++it) {
+      solve_any(h, r.p, x, nrhs, ld, trans, true);
+      stencil_apply(c, h->n, nrhs, h->coef.p, x, ld, b, r.p, -1.0, 1.0, nrm.p);
+      ACR_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+      ACR_CUDA(cudaStreamSynchronize(c.st));
+      bool all_ok = true, finite = true;
+      for (int k = 0; k < nrhs; ++k) {
+        rel[k] = hn[2 * k + 1] > 0 ? std::sqrt(hn[2 * k] / hn[2 * k + 1]) : std::sqrt(hn[2 * k]);
+        if (!(rel[k] <= rtol)) all_ok = false;  // NaN counts as not converged
+        if (!std::isfinite(rel[k])) finite = false;
+      }
+      if (all_ok) { conv = true; break; }
+      if (!finite) break;
+    }
+    if (it > maxit) it = maxit;
+    if (rel_res) std::memcpy(rel_res, rel.data(), nrhs * sizeof(double));
+    h->stats.kernel_launches = h->ctx.launches;
+    publish_profile(h);
+  });
+  if (iters) *iters = it;
+  if (st != ACR_OK) return st;
+  return conv ? ACR_OK : ACR_ERR_NOT_CONVERGED;
+}
+
+
 namespace acr {
 int handle_residual_view(acr_handle h, cudaStream_t* st, int* n, const double** coef) {
   if (!h || !h->coef.p) return ACR_ERR_ARG;
@@ -690,40 +729,20 @@ int acr_residual(acr_handle h, const double* b, const double* x, double* r, int 
 
 int acr_solve_ir(acr_handle h, const double* b, double* x, int nrhs, long ld, double rtol, int maxit, int* iters,
                  double* rel_res) {
-  if (!h || !b || !x || nrhs < 1 || maxit < 1 || ld < (long)h->n * h->n * h->n || b == x) return ACR_ERR_ARG;
-  bool conv = false;
-  int it = 0;
-  int st = guard([&] {
-    Ctx& c = h->ctx;
-    h->ctx.launches = 0;
-    const long N = (long)h->n * h->n * h->n;
-    DBuf<double> r(c, (size_t)ld * nrhs), nrm(c, 2 * (size_t)nrhs);
-    ACR_CUDA(cudaMemset2DAsync(x, ld * sizeof(double), 0, N * sizeof(double), nrhs, c.st));
-    ACR_CUDA(cudaMemcpy2DAsync(r.p, ld * sizeof(double), b, ld * sizeof(double), N * sizeof(double), nrhs,
-                               cudaMemcpyDeviceToDevice, c.st));
-    std::vector<double> hn(2 * nrhs), rel(nrhs, 1.0);
-    for (it = 1; it <= maxit; ++it) {
-      solve_any(h, r.p, x, nrhs, ld, false, true);
-      stencil_apply(c, h->n, nrhs, h->coef.p, x, ld, b, r.p, -1.0, 1.0, nrm.p);
-      ACR_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, c.st));
-      ACR_CUDA(cudaStreamSynchronize(c.st));
-      bool all_ok = true, finite = true;
-      for (int k = 0; k < nrhs; ++k) {
-        rel[k] = hn[2 * k + 1] > 0 ? std::sqrt(hn[2 * k] / hn[2 * k + 1]) : std::sqrt(hn[2 * k]);
-        if (!(rel[k] <= rtol)) all_ok = false;  // NaN counts as not converged
-        if (!std::isfinite(rel[k])) finite = false;
-      }
-      if (all_ok) { conv = true; break; }
-      if (!finite) break;
-    }
-    if (it > maxit) it = maxit;
-    if (rel_res) std::memcpy(rel_res, rel.data(), nrhs * sizeof(double));
-    h->stats.kernel_launches = h->ctx.launches;
-    publish_profile(h);
+  return solve_ir_impl(h, b, x, nrhs, ld, rtol, maxit, iters, rel_res, false);
+}
+
+int acr_solve_ir_transpose(acr_handle h, const double* b, double* x, int nrhs, long ld, double rtol, int maxit,
+                           int* iters, double* rel_res) {
+  return solve_ir_impl(h, b, x, nrhs, ld, rtol, maxit, iters, rel_res, true);
+}
+
+int acr_grad_logkappa(acr_handle h, const double* u, const double* lam, double* grad, int nrhs, long ld) {
+  if (!h || !u || !lam || !grad || nrhs < 1 || ld < (long)h->n * h->n * h->n) return ACR_ERR_ARG;
+  return guard([&] {
+    grad_logkappa(h->ctx, h->n, nrhs, h->kappa.p, u, lam, ld, grad, 0);
+    ACR_CUDA(cudaStreamSynchronize(h->ctx.st));
   });
-  if (iters) *iters = it;
-  if (st != ACR_OK) return st;
-  return conv ? ACR_OK : ACR_ERR_NOT_CONVERGED;
 }
 
 int acr_solve_fgmres(acr_handle h, const double* b, double* x, int nrhs, long ld, double rtol, int restart, int maxit,

@@ -188,6 +188,8 @@ template <class T> void expand_leaves(Ctx& c, int m, int b, const T* leaf, T* de
 void exp_inplace(Ctx& c, double* p, long n);
 void stencil_norms_scratch(cudaStream_t st, int n, int nrhs, const double* coef, const double* x, long ld,
                            const double* y, double* out, double* part, int nb_max, double* pairs);
+void grad_logkappa(Ctx& c, int n, int nrhs, const double* kap, const double* u, const double* lam, long ld,
+                   double* grad, int accumulate);
 void face_coefficients(Ctx& c, int n, const double* kappa, double shift, double* coef);
 void col_dots(Ctx& c, long N, int nrhs, const double* x, long ldx, const double* y, long ldy, double* out);
 void col_axpy(Ctx& c, long N, int nrhs, const double* a /*device nrhs*/, const double* x, long ldx,

@@ -499,6 +499,45 @@ void stencil_norms_scratch(cudaStream_t st, int n, int nrhs, const double* coef,
   k_reduce_pairs<<<nrhs, 256, 0, st>>>(nrhs, nb, part, pairs);
 }
 
+// dL/dg_p = -kappa_p * sum over columns of lambda^T (dA/dkappa_p) u, with
+// dc_pq/dkappa_p = 2 kappa_q^2 / ((kappa_p + kappa_q)^2 h^2) on interior faces
+// and 1/h^2 on boundary faces (u = 0 outside).  One thread per node.
+__global__ void k_grad_logkappa(int n, int nrhs, const double* __restrict__ kap, const double* __restrict__ u,
+                                const double* __restrict__ lam, long ld, double* grad, int accumulate) {
+  const long N = (long)n * n * n;
+  const int m = n * n;
+  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x) {
+    const int xi = (int)(p % n), yi = (int)((p / n) % n), zi = (int)(p / m);
+    const double kp = kap[p];
+    const long nb[6] = {xi > 0 ? p - 1 : -1, xi < n - 1 ? p + 1 : -1, yi > 0 ? p - n : -1,
+                        yi < n - 1 ? p + n : -1, zi > 0 ? p - m : -1, zi < n - 1 ? p + m : -1};
+    double acc = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+      const double up = u[(long)c * ld + p], lp = lam[(long)c * ld + p];
+      for (int d = 0; d < 6; ++d) {
+        const long q = nb[d];
+        if (q < 0) {
+          acc += lp * up * ih2;
+        } else {
+          const double kq = kap[q];
+          const double dc = 2.0 * kq * kq / ((kp + kq) * (kp + kq)) * ih2;
+          acc += dc * (lp - lam[(long)c * ld + q]) * (up - u[(long)c * ld + q]);
+        }
+      }
+    }
+    const double v = -kp * acc;
+    grad[p] = accumulate ? grad[p] + v : v;
+  }
+}
+void grad_logkappa(Ctx& c, int n, int nrhs, const double* kap, const double* u, const double* lam, long ld,
+                   double* grad, int accumulate) {
+  long N = (long)n * n * n;
+  c.kbegin();
+  k_grad_logkappa<<<nblk(N), 256, 0, c.st>>>(n, nrhs, kap, u, lam, ld, grad, accumulate);
+  c.kend(KC_STENCIL, 40.0 * N * nrhs, 8.0 * (N + 2.0 * N * nrhs + N));
+}
+
 __global__ void k_col_dots(long N, const double* x, long ldx, const double* y, long ldy, double* part) {
   int col = blockIdx.y;
   __shared__ double s1[256];

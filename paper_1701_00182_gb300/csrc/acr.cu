@@ -166,9 +166,7 @@ struct acr_handle_s {
     cutq.clear();
     kappa.release();
     coef.release();
-    if (ctx.d_flag) cudaFree(ctx.d_flag);
     if (ctx.st) cudaStreamSynchronize(ctx.st);
-    if (own_stream) cudaStreamDestroy(own_stream);
     const char* ps = std::getenv("ACR_PROFILE_SITES");
     if (ps && ps[0] == '1' && !ctx.site.empty()) {
       ctx.kflush();
@@ -177,8 +175,17 @@ struct acr_handle_s {
                      kv.second.second / 1e12);
     }
     for (auto& p : ctx.pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    ctx.pend.clear();
     for (auto e : ctx.evfree) cudaEventDestroy(e);
-    if (ctx.st) cudaStreamSynchronize(ctx.st);
+    ctx.evfree.clear();
+    if (ctx.d_flag) cudaFree(ctx.d_flag);
+    ctx.d_flag = nullptr;
+    // The private stream goes last, and no call may name it afterwards.
+    if (own_stream) {
+      cudaStreamDestroy(own_stream);
+      own_stream = nullptr;
+      ctx.st = nullptr;
+    }
   }
 };
 

@@ -190,3 +190,5 @@ def test_solve_graphs_replay_bit_identical(acr):
     itg, relg, _ = acr.acr_solve_ir(hg, b, xg, rtol=1e-10)
     assert ite == itg and max(relg) <= 1e-10
     np.testing.assert_array_equal(from_cols(xg), from_cols(xe))
+    hg.close()  # a handle with a private stream and captured graphs tears down cleanly
+    he.close()

@@ -65,6 +65,10 @@ typedef struct {
   void* cuda_stream;      /* cudaStream_t to run on; NULL = legacy default stream */
   int profile;            /* 1 = time every kernel launch with CUDA events (per-class totals in acr_stats) */
   int inverse_fp64;       /* ACR_FP32 only: 1 = leaf and Woodbury-coupling inverses computed in FP64 */
+  int tensor_cores;       /* ACR_FP32 only: 1 = large GEMM tiles on the tensor pipe with a 3xTF32 split
+                             (FP32-level accuracy) instead of FP32 FMA */
+  int coarse_dense_max;   /* coarsest plane factorised densely in FP64 when n^2 <= this (0 = default 4096,
+                             negative = never; otherwise it is inverted as a HODLR matrix) */
   int graphs;             /* 1 = capture the solve sweeps once per (nrhs, transpose) as a CUDA graph and replay
                              it; with cuda_stream NULL the handle then runs on its own blocking stream */
 } acr_opts;
@@ -91,6 +95,7 @@ typedef struct {
   long long kc_launches[16];
   int jacobi_sweeps_max;                  /* most Jacobi sweeps any core SVD of the factorisation needed */
   int graphs_captured;                    /* solve graphs captured so far */
+  int coarse_dense;                       /* 1 if the coarsest plane has a dense FP64 inverse */
 } acr_stats;
 
 /* Default options (FP64, shift 0, unlimited ranks and memory, autotune off, nrhs_max 64). */

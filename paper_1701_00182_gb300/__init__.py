@@ -45,6 +45,8 @@ class AcrOpts(C.Structure):
         ("cuda_stream", C.c_void_p),
         ("profile", C.c_int),
         ("inverse_fp64", C.c_int),
+        ("tensor_cores", C.c_int),
+        ("coarse_dense_max", C.c_int),
         ("graphs", C.c_int),
     ]
 
@@ -71,6 +73,7 @@ class AcrStats(C.Structure):
         ("kc_launches", C.c_longlong * 16),
         ("jacobi_sweeps_max", C.c_int),
         ("graphs_captured", C.c_int),
+        ("coarse_dense", C.c_int),
     ]
 
 
@@ -320,6 +323,7 @@ def acr_get_stats(h: Handle) -> dict:
         "kernel_launches": s.kernel_launches,
         "jacobi_sweeps_max": s.jacobi_sweeps_max,
         "graphs_captured": s.graphs_captured,
+        "coarse_dense": s.coarse_dense,
         "kernels": {nm: {"ms": s.kc_ms[i], "flops": s.kc_flops[i], "bytes": s.kc_bytes[i],
                          "launches": s.kc_launches[i]} for i, nm in enumerate(KERNEL_CLASSES)},
     }

@@ -132,6 +132,7 @@ struct FactorT {
   int q = 0;
   std::vector<LevelF<T>> lv;
   HStore<T> Xc;
+  DBuf<double> Xdense;  // FP64 dense inverse of the coarsest plane (m <= coarse_dense_max)
   DBuf<T> Fint, tmp;
   int cap = 0;
   std::vector<std::pair<long, cudaGraphExec_t>> graphs;  // key nrhs*2 + transpose
@@ -146,7 +147,7 @@ using namespace acr;
 
 struct acr_handle_s {
   Ctx ctx;
-  int n = 0, leaf = 0, precision = ACR_FP64, nrhs_max = 64, max_rank = 0;
+  int n = 0, leaf = 0, precision = ACR_FP64, nrhs_max = 64, max_rank = 0, coarse_dense_max = 4096;
   bool graphs = false;
   cudaStream_t own_stream = nullptr;
   double tol = 0, shift = 0;
@@ -180,6 +181,8 @@ struct acr_handle_s {
     ctx.evfree.clear();
     if (ctx.d_flag) cudaFree(ctx.d_flag);
     ctx.d_flag = nullptr;
+    if (ctx.d_jflops) cudaFree(ctx.d_jflops);
+    ctx.d_jflops = nullptr;
     // The private stream goes last, and no call may name it afterwards.
     if (own_stream) {
       cudaStreamDestroy(own_stream);
@@ -222,6 +225,22 @@ void check_flag(acr_handle_s* h) {
 
 void max_into(int* dst, const int* src, int L) {
   for (int l = 0; l < L; ++l) dst[l] = std::max(dst[l], src[l]);
+}
+
+// Dense m x m image (row major, permuted order) of one HODLR matrix.
+template <class T>
+void expand_dense_device(Ctx& c, const HMat<T>& A1, T* d) {
+  const int m = A1.m, b = A1.b, L = A1.L;
+  ACR_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * (size_t)m * m, c.st));
+  expand_leaves<T>(c, m, b, A1.leaf, d);
+  for (int l = 0; l < L; ++l) {
+    const int K = A1.K[l];
+    if (!K) continue;
+    const int s = m >> (l + 1), nclus = 1 << (l + 1);
+    c.tag = "expand";
+    gemm<T>(c, s, s, K, 1, nclus, T(1), opm<T>(A1.U[l], K, 1, 0, (long)s * K),
+            opm<T>(A1.V[l], 1, K, 0, (long)s * K, 1), T(0), opm<T>(d + s, m, 1, 0, (long)s * m + s, 0, 0, -2L * s));
+  }
 }
 
 template <class T>
@@ -314,7 +333,17 @@ void factor_impl(acr_handle_s* h, FactorT<T>& fac) {
     if (r < 16) h->stats.t_level_ms[r] = ms;
     ++r;
   }
-  {
+  if (m <= h->coarse_dense_max) {
+    // Coarsest plane small enough for a dense FP64 factorisation (Eq. first_backSubs).
+    DBuf<T> dT(c, (size_t)m * m);
+    expand_dense_device<T>(c, D.h, dT.p);
+    DBuf<double> dD(c, (size_t)m * m);
+    convert<T, double>(c, (long)m * m, dT.p, dD.p);
+    dT.release();
+    fac.Xdense = DBuf<double>(c, (size_t)m * m);
+    dense_inverse_fp64(c, m, dD.p, fac.Xdense.p);
+    h->stats.coarse_dense = 1;
+  } else {
     int rk[MAXL] = {};
     WSum<T> ws = winverse<T>(c, D.h);
     fac.Xc = wsum_to_hodlr<T>(c, ws, tol, exact, rk);
@@ -331,9 +360,26 @@ void factor_impl(acr_handle_s* h, FactorT<T>& fac) {
 
 template <class T>
 long factor_bytes(const FactorT<T>& f) {
-  long s = f.Xc.h.bytes();
+  long s = f.Xc.h.bytes() + (long)f.Xdense.n * 8;
   for (auto& l : f.lv) s += l.X.h.bytes() + l.E.h.bytes() + l.F.h.bytes() + l.G.h.bytes() + l.H.h.bytes();
   return s;
+}
+
+// Coarsest plane: last <- X_c last (or X_c^T), through the HODLR inverse or
+// the dense FP64 inverse.
+template <class T>
+void coarse_apply(Ctx& c, FactorT<T>& fac, Pan<T> last, Pan<T> tp, int m, int nrhs, bool trans) {
+  if (fac.Xdense.p) {
+    DBuf<double> f64(c, (size_t)m * nrhs), y64(c, (size_t)m * nrhs);
+    convert<T, double>(c, (long)m * nrhs, last.p, f64.p);
+    c.tag = "coarse";
+    gemm<double>(c, m, nrhs, m, 1, 1, 1.0, opm<double>(fac.Xdense.p, trans ? 1 : m, trans ? m : 1, 0, 0),
+                 opm<double>(f64.p, nrhs, 1, 0, 0), 0.0, opm<double>(y64.p, nrhs, 1, 0, 0));
+    convert<double, T>(c, (long)m * nrhs, y64.p, last.p);
+  } else {
+    hmatvec<T>(c, fac.Xc.h, 0, trans, last, tp, nrhs, T(1), T(0));
+    copy2d<T>(c, 1, m, nrhs, T(1), tp.p, nrhs, 0, last.p, nrhs, 0);
+  }
 }
 
 // The forward-reduction / coarsest / back-substitution sweeps on the
@@ -355,8 +401,7 @@ void sweeps(acr_handle_s* h, FactorT<T>& fac, T* Fint, T* tmp, int nrhs, bool tr
       hmatvec<T>(c, lv.G.h, 0, false, view(r, 0), view(r, 1), nrhs, T(-1), T(1));
       if (lv.ne > 1) hmatvec<T>(c, lv.H.h, 0, false, view(r, 2), view(r, 1), nrhs, T(-1), T(1));
     }
-    hmatvec<T>(c, fac.Xc.h, 0, false, last, tp, nrhs, T(1), T(0));
-    copy2d<T>(c, 1, m, nrhs, T(1), tmp, nrhs, 0, last.p, nrhs, 0);
+    coarse_apply<T>(c, fac, last, tp, m, nrhs, false);
     for (int r = q - 1; r >= 0; --r) {
       LevelF<T>& lv = fac.lv[r];
       const int ne = lv.ne;
@@ -376,8 +421,7 @@ void sweeps(acr_handle_s* h, FactorT<T>& fac, T* Fint, T* tmp, int nrhs, bool tr
       if (ne > 1) hmatvec<T>(c, lv.E.h.sub(2, 2, ne - 1), 0, true, view(r, 2), view(r, 1), nrhs, T(-1), T(1));
       hmatvec<T>(c, lv.F.h.sub(0, 2, ne), 0, true, view(r, 0), view(r, 1), nrhs, T(-1), T(1));
     }
-    hmatvec<T>(c, fac.Xc.h, 0, true, last, tp, nrhs, T(1), T(0));
-    copy2d<T>(c, 1, m, nrhs, T(1), tmp, nrhs, 0, last.p, nrhs, 0);
+    coarse_apply<T>(c, fac, last, tp, m, nrhs, true);
     for (int r = q - 1; r >= 0; --r) {
       LevelF<T>& lv = fac.lv[r];
       const int ne = lv.ne;
@@ -445,6 +489,11 @@ void solve_impl(acr_handle_s* h, FactorT<T>& fac, const double* rhs, double* x, 
 
 void publish_profile(acr_handle_s* h) {
   h->ctx.kflush();
+  if (h->ctx.d_jflops) {
+    double jf = 0;
+    if (cudaMemcpy(&jf, h->ctx.d_jflops, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess)
+      h->ctx.kc_flops[KC_JACOBI] = jf;
+  }
   for (int k = 0; k < KC_N; ++k) {
     h->stats.kc_ms[k] = h->ctx.kc_ms[k];
     h->stats.kc_flops[k] = h->ctx.kc_flops[k];
@@ -482,7 +531,17 @@ void expand_block(acr_handle_s* h, const HMat<T>& A1, double* dense_host) {
 template <class T>
 void get_block_impl(acr_handle_s* h, FactorT<T>& f, int which, int level, int index, double* dense) {
   if (which == 5) {
-    expand_block<T>(h, f.Xc.h.sub(0, 1, 1), dense);
+    if (f.Xdense.p) {
+      const int m = h->geo.m;
+      std::vector<double> hb((size_t)m * m);
+      ACR_CUDA(cudaMemcpyAsync(hb.data(), f.Xdense.p, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, h->ctx.st));
+      ACR_CUDA(cudaStreamSynchronize(h->ctx.st));
+      const std::vector<int>& pm = h->geo.perm;
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) dense[(size_t)pm[i] * m + pm[j]] = hb[(size_t)i * m + j];
+    } else {
+      expand_block<T>(h, f.Xc.h.sub(0, 1, 1), dense);
+    }
     return;
   }
   if (level < 0 || level >= (int)f.lv.size()) throw AcrError(ACR_ERR_ARG, "level out of range");
@@ -616,8 +675,11 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     c.autotune = o.autotune != 0;
     c.profile = o.profile != 0;
     c.inverse_fp64 = o.inverse_fp64 != 0;
+    c.tensor = o.tensor_cores != 0;
     ACR_CUDA(cudaMalloc(&c.d_flag, 4 * sizeof(int)));
     ACR_CUDA(cudaMemsetAsync(c.d_flag, 0, 4 * sizeof(int), c.st));
+    ACR_CUDA(cudaMalloc(&c.d_jflops, sizeof(double)));
+    ACR_CUDA(cudaMemsetAsync(c.d_jflops, 0, sizeof(double), c.st));
     h->n = n;
     h->leaf = leaf;
     h->tol = tol;
@@ -625,6 +687,7 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     h->precision = o.precision;
     h->nrhs_max = o.nrhs_max;
     h->max_rank = o.max_rank;
+    h->coarse_dense_max = o.coarse_dense_max > 0 ? o.coarse_dense_max : (o.coarse_dense_max < 0 ? 0 : 4096);
     const Geometry& g = h->geo;
     const long N = (long)n * n * n;
     h->perm = DBuf<int>(c, g.m);

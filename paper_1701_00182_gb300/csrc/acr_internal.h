@@ -47,6 +47,7 @@ enum KClass { KC_GEMM, KC_SPLITK, KC_QR, KC_PCHOL, KC_JACOBI, KC_COEF, KC_GJ, KC
 struct Ctx {
   cudaStream_t st = nullptr;
   int* d_flag = nullptr;            // device status flags (breakdown ...)
+  double* d_jflops = nullptr;       // device count of Jacobi SVD flops (pair evaluations + rotations)
   long long launches = 0;
   long long gemm_flops = 0;
   size_t live_bytes = 0, peak_bytes = 0, budget = 0;
@@ -54,7 +55,8 @@ struct Ctx {
   std::vector<std::pair<unsigned long long, int>> tuned;  // shape key -> config
   std::map<uintptr_t, size_t> live;  // allocation start -> bytes (for the operand extent check)
   bool check_bounds = false;
-  bool inverse_fp64 = false;         // FP32 factorisation: leaf and coupling inverses in FP64         // ACR_CHECK_BOUNDS=1: verify every GEMM operand range on the host
+  bool inverse_fp64 = false;
+  bool tensor = false;               // FP32 GEMMs of large tiles on the tensor pipe (3xTF32)         // FP32 factorisation: leaf and coupling inverses in FP64         // ACR_CHECK_BOUNDS=1: verify every GEMM operand range on the host
   void check_range(const void* base, long lo, long hi, size_t es, const char* what) const;
   bool profile = false;  // record CUDA events around every launch, accumulated per kernel class
   double kc_ms[16] = {}, kc_flops[16] = {}, kc_bytes[16] = {};
@@ -196,6 +198,10 @@ void col_axpy(Ctx& c, long N, int nrhs, const double* a /*device nrhs*/, const d
               double* y, long ldy);
 void col_scale_copy(Ctx& c, long N, int nrhs, const double* a, const double* x, long ldx, double* y,
                     long ldy);
+
+// ---- dense coarsest plane (coarse.cu) ---------------------------------------
+void dense_inverse_fp64(Ctx& c, int m, double* A, double* Xinv);
+template <class S, class D> void convert(Ctx& c, long n, const S* a, D* b);
 
 // ---- recompression (recompress.cu) ----------------------------------------
 // Level-l recompression of the off-diagonal blocks  Left|c * Right|c^1 ^T  for

@@ -240,6 +240,142 @@ __global__ void __launch_bounds__(256) k_gemm_f32_big(GArgs<float> g) {
   }
 }
 
+// ---- 3xTF32 tensor-core tile --------------------------------------------------
+// FP32 GEMM on the tensor pipe: every operand x is split into a TF32 head
+// h = tf32(x) and tail l = tf32(x - h), and a*b is accumulated in FP32 as
+// a_l b_h + a_h b_l + a_h b_h (the a_l b_l term is below FP32 rounding), which
+// keeps FP32-level accuracy.  mma.sync m16n8k8 (row.col), 128 x 128 x 16 tile,
+// 8 warps of 64 x 32, double-buffered shared memory.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(256) k_gemm_tf32x3(GArgs<float> g) {
+  constexpr int BM = 128, BN = 128, BK = 16, PAD = 8;
+  __shared__ __align__(16) float As[2][BK][BM + PAD];
+  __shared__ __align__(16) float Bs[2][BK][BN + PAD];
+  const int bi = blockIdx.x;
+  const int plane = bi / g.nclus, c = bi - plane * g.nclus;
+  const int tilesN = (g.N + BN - 1) / BN;
+  const int m0 = (blockIdx.y / tilesN) * BM, n0 = (blockIdx.y % tilesN) * BN;
+  if (g.sym && m0 >= n0 + BN) return;
+  const int kbeg = blockIdx.z * g.kchunk;
+  const int kend = min(g.K, kbeg + g.kchunk);
+  const float* __restrict__ A = opaddr(g.A, plane, c);
+  const float* __restrict__ B = opaddr(g.B, plane, c);
+  const long ars = g.A.rs, acs = g.A.cs, brs = g.B.rs, bcs = g.B.cs;
+  const bool a_kfast = (acs == 1), b_nfast = (bcs == 1);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;  // warp tile origin
+  const int gq = lane >> 2, tq = lane & 3;                  // groupID, thread in group
+  float ra[8], rb[8];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      int e = tid + 256 * u;
+      int ii, kk;
+      if (a_kfast) { ii = e >> 4; kk = e & 15; } else { ii = e & 127; kk = e >> 7; }
+      int gi = m0 + ii, gk = k0 + kk;
+      ra[u] = (gi < g.M && gk < kend) ? A[(long)gi * ars + (long)gk * acs] : 0.f;
+      int jj, kb;
+      if (b_nfast) { jj = e & 127; kb = e >> 7; } else { jj = e >> 4; kb = e & 15; }
+      int gj = n0 + jj, gk2 = k0 + kb;
+      rb[u] = (gk2 < kend && gj < g.N) ? B[(long)gk2 * brs + (long)gj * bcs] : 0.f;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      int e = tid + 256 * u;
+      int ii, kk;
+      if (a_kfast) { ii = e >> 4; kk = e & 15; } else { ii = e & 127; kk = e >> 7; }
+      As[buf][kk][ii] = ra[u];
+      int jj, kb;
+      if (b_nfast) { jj = e & 127; kb = e >> 7; } else { jj = e >> 4; kb = e & 15; }
+      Bs[buf][kb][jj] = rb[u];
+    }
+  };
+  float acc[4][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+  int buf = 0;
+  if (kbeg < kend) {
+    fetch(kbeg);
+    stash(0);
+  }
+  __syncthreads();
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool more = k0 + BK < kend;
+    if (more) fetch(k0 + BK);
+#pragma unroll
+    for (int ks = 0; ks < BK; ks += 8) {
+      uint32_t ah[4][4], al[4][4], bh[4][2], bl[4][2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int mr = wm + 16 * i + gq;
+        split_tf32(As[buf][ks + tq][mr], ah[i][0], al[i][0]);
+        split_tf32(As[buf][ks + tq][mr + 8], ah[i][1], al[i][1]);
+        split_tf32(As[buf][ks + tq + 4][mr], ah[i][2], al[i][2]);
+        split_tf32(As[buf][ks + tq + 4][mr + 8], ah[i][3], al[i][3]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int nc = wn + 8 * j + gq;
+        split_tf32(Bs[buf][ks + tq][nc], bh[j][0], bl[j][0]);
+        split_tf32(Bs[buf][ks + tq + 4][nc], bh[j][1], bl[j][1]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          mma_tf32(acc[i][j], al[i], bh[j]);
+          mma_tf32(acc[i][j], ah[i], bl[j]);
+          mma_tf32(acc[i][j], ah[i], bh[j]);
+        }
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  float* P = g.partial ? g.partial + ((long)blockIdx.z * g.batch + bi) * (long)g.M * g.N : nullptr;
+  float* C = g.partial ? nullptr : opaddr(g.C, plane, c);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gi = m0 + wm + 16 * i + gq + ((q & 2) ? 8 : 0);
+        const int gj = n0 + wn + 8 * j + 2 * tq + (q & 1);
+        if (gi >= g.M || gj >= g.N) continue;
+        if (P) {
+          P[(long)gi * g.N + gj] = acc[i][j][q];
+        } else {
+          float* cp = C + (long)gi * g.C.rs + (long)gj * g.C.cs;
+          float v = g.alpha * acc[i][j][q];
+          if (g.beta != 0.f) v += g.beta * *cp;
+          *cp = v;
+        }
+      }
+}
+
 template <class T>
 __global__ void k_splitk_reduce(GArgs<T> g, int nsplit) {
   long tot = (long)g.batch * g.M * g.N;
@@ -290,7 +426,7 @@ namespace {
 struct Cfg {
   int bm, bn, bk;
 };
-constexpr Cfg kCfg[5] = {{64, 64, 16}, {128, 64, 8}, {32, 32, 32}, {128, 128, 8}, {128, 128, 8}};
+constexpr Cfg kCfg[6] = {{64, 64, 16}, {128, 64, 8}, {32, 32, 32}, {128, 128, 8}, {128, 128, 8}, {128, 128, 16}};
 
 template <class T>
 void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st) {
@@ -299,16 +435,20 @@ void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st) {
     case 1: k_gemm<T, 128, 64, 8, 8, 4><<<grid, 256, 0, st>>>(g); break;
     case 2: k_gemm<T, 32, 32, 32, 2, 2><<<grid, 256, 0, st>>>(g); break;
     case 3: k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g); break;
-    default:
+    case 4:
       if constexpr (sizeof(T) == 4) k_gemm_f32_big<<<grid, 256, 0, st>>>(g);
+      else k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g);
+      break;
+    default:
+      if constexpr (sizeof(T) == 4) k_gemm_tf32x3<<<grid, 256, 0, st>>>(g);
       else k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g);
       break;
   }
 }
 
-int heuristic_cfg(int M, int N, long batch, int es) {
+int heuristic_cfg(int M, int N, long batch, int es, bool tensor) {
   if (M <= 32 && N <= 32) return 2;
-  if (M >= 96 && N >= 96) return es == 4 ? 4 : 3;
+  if (M >= 96 && N >= 96) return es == 4 ? (tensor ? 5 : 4) : 3;
   if (M >= 128 && N <= 64) return 1;
   return 0;
 }
@@ -409,7 +549,7 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
   if (batch > 0x7fffffffL) throw AcrError(1, "gemm batch too large");
   c.gemm_flops += (sym ? 1LL * M * (N + 1) : 2LL * M * N) * K * batch;
   GArgs<T> g{M, N, K, nclus, (int)batch, alpha, beta, A, B, C, K, nullptr, sym};
-  int cfg = heuristic_cfg(M, N, batch, (int)sizeof(T));
+  int cfg = heuristic_cfg(M, N, batch, (int)sizeof(T), c.tensor);
   int split = split_for(cfg, M, N, K, batch);
   if (c.autotune) {
     unsigned long long key = shape_key(sizeof(T), M, N, K, batch);
@@ -432,10 +572,11 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
       ACR_CUDA(cudaEventCreate(&e1));
       float best = 1e30f;
       int bestc = 0;
-      for (int cand = 0; cand < 10; ++cand) {
-        int cf = cand % 5;
-        int sp = (cand / 5) ? split_for(cf, M, N, K, batch) : 1;
-        if ((cand / 5) && sp == 1) continue;
+      for (int cand = 0; cand < 12; ++cand) {
+        int cf = cand % 6;
+        if (cf == 5 && !(c.tensor && sizeof(T) == 4)) continue;
+        int sp = (cand / 6) ? split_for(cf, M, N, K, batch) : 1;
+        if ((cand / 6) && sp == 1) continue;
         run_gemm<T>(c, cf, sp, M, N, K, batch, gt);  // warm
         ACR_CUDA(cudaEventRecord(e0, c.st));
         run_gemm<T>(c, cf, sp, M, N, K, batch, gt);
@@ -452,8 +593,8 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tuned.push_back({key, found});
     }
-    cfg = found % 5;
-    split = (found / 5) ? split_for(cfg, M, N, K, batch) : 1;
+    cfg = found % 6;
+    split = (found / 6) ? split_for(cfg, M, N, K, batch) : 1;
   }
   run_gemm<T>(c, cfg, split, M, N, K, batch, g);
   if (sym) {

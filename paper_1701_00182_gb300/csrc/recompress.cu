@@ -294,7 +294,8 @@ constexpr int kJacThreads = 1024;
 template <class T>
 __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, const int* kk, long NB, T* Wall, T* Vall,
                                                         T* Xall, T* Yall, T* sigall, int* rankall, T tol,
-                                                        int maxsweeps, int smem_elems, int* sweeps_out) {
+                                                        int maxsweeps, int smem_elems, int* sweeps_out,
+                                                        double* flops_out) {
   extern __shared__ unsigned char smraw[];
   T* sig = reinterpret_cast<T*>(smraw);
   int* ord = reinterpret_cast<int*>(sig + r);
@@ -303,7 +304,10 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
   const long bi = blockIdx.x;
   const T* C = Call + bi * (long)r * r;
   const int kL = kk[bi], kR = kk[NB + bi];
-  const int trans = kL < kR;
+  // Orthogonalise the rows of C: they are graded (row t carries the t-th
+  // pivoted-Cholesky row of the left factor, whose norms decrease), and
+  // one-sided Jacobi converges in far fewer sweeps on graded columns.
+  const int trans = 1;
   const int nrow = trans ? kR : kL, ncol = trans ? kL : kR;
   const bool insm = (long)nrow * ncol <= smem_elems;
   const long ldw = insm ? nrow : r;
@@ -349,20 +353,27 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
   const T tau = fmax(T(1e-4) * tol * tol, T(16) * unit * unit);
   const T floor2 = tau * fro2;
   const int ne = ncol + (ncol & 1);
+  long long nevals = 0, nrots = 0;  // per warp (identical on its lanes)
   for (int sw = 0; sw < maxsweeps && ne > 1; ++sw) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int step = 0; step < ne - 1; ++step) {
       for (int k = warp; k < ne / 2; k += nw) {
+        // Round-robin tournament: position 0 fixed, positions 1..ne-1 rotate.
         int i, jx;
         if (k == 0) {
           i = 0;
-          jx = 1 + step % (ne - 1);
+          jx = 1 + step;
         } else {
-          i = 1 + (step + k) % (ne - 1);
-          jx = 1 + ((step - k) % (ne - 1) + (ne - 1)) % (ne - 1);
+          int a = step + k;
+          if (a >= ne - 1) a -= ne - 1;
+          int b = step - k;
+          if (b < 0) b += ne - 1;
+          i = 1 + a;
+          jx = 1 + b;
         }
         if (i >= ncol || jx >= ncol) continue;
+        ++nevals;
         T* wi = W + (long)i * ldw;
         T* wj = W + (long)jx * ldw;
         T* vi = V + (long)i * r;
@@ -400,7 +411,10 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
             rotd = true;
           }
         }
-        if (rotd && lane == 0) s_rot = 1;
+        if (rotd) {
+          ++nrots;
+          if (lane == 0) s_rot = 1;
+        }
       }
       __syncthreads();
     }
@@ -409,6 +423,8 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
     if (tid == 0 && sweeps_out) atomicMax(sweeps_out, sw + 1);
     if (!rot) break;
   }
+  if (lane == 0 && flops_out && (nevals | nrots))
+    atomicAdd(flops_out, 6.0 * (double)nevals * nrow + 6.0 * (double)nrots * (nrow + ncol));
   for (int col = warp; col < ncol; col += nw) {
     T a = 0;
     for (int q = lane; q < nrow; q += 32) a += W[(long)col * ldw + q] * W[(long)col * ldw + q];
@@ -568,7 +584,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     ACR_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     c.kbegin();
     k_jacobi<T><<<(unsigned)NB, kJacThreads, sm, c.st>>>(r, Cc.p, kk.p, NB, W.p, Vw.p, Xo.p, Yo.p, sig.p, rank.p,
-                                                         T(tol), 30, smem_elems, c.d_flag + 1);
+                                                         T(tol), 30, smem_elems, c.d_flag + 1, c.d_jflops);
     c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r);
   }
   std::vector<int> hr(NB);

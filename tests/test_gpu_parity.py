@@ -192,3 +192,36 @@ def test_solve_graphs_replay_bit_identical(acr):
     np.testing.assert_array_equal(from_cols(xg), from_cols(xe))
     hg.close()  # a handle with a private stream and captured graphs tears down cleanly
     he.close()
+
+
+def test_fp32_tensor_core_gemms_match_fma_path(acr):
+    """FP32 factorisation with the 3xTF32 tensor-core GEMM tiles agrees with the
+    FP32-FMA tiles to FP32-level accuracy and still refines to 1e-10."""
+    n = 32
+    g = synthetic.gaussian_random_field(n, 1)
+    f = synthetic.multi_rhs(n, [4, 5])
+    hf = acr.acr_factor(n, g, 1e-6, 32, precision=acr.ACR_FP32)
+    ht = acr.acr_factor(n, g, 1e-6, 32, precision=acr.ACR_FP32, tensor_cores=1)
+    Xf = acr.acr_get_factor_block(hf, 0, 0, 3)
+    Xt = acr.acr_get_factor_block(ht, 0, 0, 3)
+    assert rel(Xt, Xf) < 1e-4
+    b = to_cols(f)
+    x = empty_like_cols(b)
+    it, relr, _ = acr.acr_solve_ir(ht, b, x, rtol=1e-10, maxit=40)
+    assert max(relr) <= 1e-10
+    assert np.all(iterative.rel_residual(n, g, from_cols(x), f) <= 1.01e-10)
+
+
+@pytest.mark.parametrize("coarse_dense_max,dense", [(0, 1), (-1, 0)])
+def test_coarsest_plane_dense_fp64_and_hodlr(acr, coarse_dense_max, dense):
+    """The coarsest block is factorised densely in FP64 (default for n^2 <= 4096)
+    or inverted as a HODLR matrix; both reach the oracle's coarsest inverse."""
+    n = 16
+    g = synthetic.gaussian_random_field(n, 8)
+    D, E, F = op.plane_blocks(n, g)
+    fac = cr.cr_factor(D, E, F)
+    h = acr.acr_factor(n, g, 0.0, 32, coarse_dense_max=coarse_dense_max)
+    assert acr.acr_get_stats(h)["coarse_dense"] == dense
+    assert rel(acr.acr_get_factor_block(h, 5, 0, 0), np.linalg.inv(fac.coarse_D)) < 1e-12
+    f = synthetic.uniform_rhs(n, 3)
+    assert rel(_solve(acr, h, f), direct.dense_solve(n, g, f)) < 1e-12

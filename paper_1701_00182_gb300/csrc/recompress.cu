@@ -304,10 +304,10 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
   const long bi = blockIdx.x;
   const T* C = Call + bi * (long)r * r;
   const int kL = kk[bi], kR = kk[NB + bi];
-  // Orthogonalise the rows of C: they are graded (row t carries the t-th
-  // pivoted-Cholesky row of the left factor, whose norms decrease), and
-  // one-sided Jacobi converges in far fewer sweeps on graded columns.
-  const int trans = 1;
+  // Orthogonalise the columns of the wider orientation (never more columns
+  // than rows).  On a tie take the rows of C: they are graded (row t carries
+  // the t-th pivoted-Cholesky row of the left factor, norms decreasing).
+  const int trans = kL <= kR;
   const int nrow = trans ? kR : kL, ncol = trans ? kL : kR;
   const bool insm = (long)nrow * ncol <= smem_elems;
   const long ldw = insm ? nrow : r;

@@ -193,6 +193,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--tensor-cores", type=int, default=1, help="3xTF32 tensor-core GEMM tiles in the FP32 path")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="acr", choices=["acr", "reference"])
     ap.add_argument("--n", type=int, default=128)
@@ -237,7 +238,8 @@ def main():
 
     def step(profile=0, kappa=g_dev, b=B, x=X, precision=prec):
         h = acr.acr_factor(n, kappa, WORKLOAD["tol"], WORKLOAD["leaf"], precision=precision, profile=profile,
-                           nrhs_max=nrhs, autotune=args.autotune, graphs=1)
+                           nrhs_max=nrhs, autotune=args.autotune, graphs=1,
+                           tensor_cores=args.tensor_cores)
         it, rel, st = acr.acr_solve_ir(h, b.T, x.T, rtol=WORKLOAD["rtol"], maxit=60, check=False)
         s = acr.acr_get_stats(h)
         h.close()

@@ -245,19 +245,22 @@ __global__ void __launch_bounds__(kCholThreads) k_pchol(int r, const T* Gall, T 
 // held in registers (lane owns rows lane + 32 q).  Returns true if rotated.
 template <class T, int RPT>
 __device__ __forceinline__ bool jacobi_pair(T* wi, T* wj, int nrow, T* vi, T* vj, int ncol, T eps, T floor2,
-                                            T* na, T* nb, int lane) {
-  const T a = *na, b = *nb;  // squared column norms, kept up to date in shared memory
-  if (fmin(a, b) <= floor2) return false;  // a negligible column: its rotation cannot matter
+                                            int lane) {
   T x[RPT], y[RPT];
-  T g = 0;
+  T a = 0, b = 0, g = 0;
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     int idx = lane + 32 * q;
     x[q] = idx < nrow ? wi[idx] : T(0);
     y[q] = idx < nrow ? wj[idx] : T(0);
+    a += x[q] * x[q];
+    b += y[q] * y[q];
     g += x[q] * y[q];
   }
+  a = warp_sum(a);
+  b = warp_sum(b);
   g = warp_sum(g);
+  if (fmin(a, b) <= floor2) return false;  // a negligible column: its rotation cannot matter
   if (!(g != T(0) && fabs(g) > eps * sqrt(a * b))) return false;
   T zeta = (b - a) / (T(2) * g);
   T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
@@ -283,11 +286,6 @@ __device__ __forceinline__ bool jacobi_pair(T* wi, T* wj, int nrow, T* vi, T* vj
       vi[idx] = cs * x[q] - sn * y[q];
       vj[idx] = sn * x[q] + cs * y[q];
     }
-  }
-  if (lane == 0) {
-    const T csg = T(2) * cs * sn * g;
-    *na = fmax(cs * cs * a - csg + sn * sn * b, T(0));
-    *nb = fmax(sn * sn * a + csg + cs * cs * b, T(0));
   }
   return true;
 }
@@ -360,12 +358,6 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
   long long nevals = 0, nrots = 0;  // per warp (identical on its lanes)
   for (int sw = 0; sw < maxsweeps && ne > 1; ++sw) {
     if (tid == 0) s_rot = 0;
-    for (int col = warp; col < ncol; col += nw) {  // exact squared norms for this sweep
-      T a = 0;
-      for (int q = lane; q < nrow; q += 32) a += W[(long)col * ldw + q] * W[(long)col * ldw + q];
-      a = warp_sum(a);
-      if (lane == 0) sig[col] = a;
-    }
     __syncthreads();
     for (int step = 0; step < ne - 1; ++step) {
       for (int k = warp; k < ne / 2; k += nw) {
@@ -389,15 +381,20 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
         T* vi = V + (long)i * r;
         T* vj = V + (long)jx * r;
         bool rotd;
-        if (nrow <= 256) rotd = jacobi_pair<T, 8>(wi, wj, nrow, vi, vj, ncol, eps, floor2, sig + i, sig + jx, lane);
+        if (nrow <= 256) rotd = jacobi_pair<T, 8>(wi, wj, nrow, vi, vj, ncol, eps, floor2, lane);
         else if (sizeof(T) == 4 && nrow <= 512)
-          rotd = jacobi_pair<T, (sizeof(T) == 4 ? 16 : 8)>(wi, wj, nrow, vi, vj, ncol, eps, floor2, sig + i,
-                                                          sig + jx, lane);
+          rotd = jacobi_pair<T, (sizeof(T) == 4 ? 16 : 8)>(wi, wj, nrow, vi, vj, ncol, eps, floor2, lane);
         else {
           rotd = false;
-          T g = 0;
-          const T a = sig[i], b = sig[jx];
-          for (int q = lane; q < nrow; q += 32) g += wi[q] * wj[q];
+          T a = 0, b = 0, g = 0;
+          for (int q = lane; q < nrow; q += 32) {
+            T x = wi[q], y = wj[q];
+            a += x * x;
+            b += y * y;
+            g += x * y;
+          }
+          a = warp_sum(a);
+          b = warp_sum(b);
           g = warp_sum(g);
           if (fmin(a, b) > floor2 && g != T(0) && fabs(g) > eps * sqrt(a * b)) {
             T zeta = (b - a) / (T(2) * g);
@@ -412,11 +409,6 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
               T x = vi[q], y = vj[q];
               vi[q] = cs * x - sn * y;
               vj[q] = sn * x + cs * y;
-            }
-            if (lane == 0) {
-              const T csg = T(2) * cs * sn * g;
-              sig[i] = fmax(cs * cs * a - csg + sn * sn * b, T(0));
-              sig[jx] = fmax(sn * sn * a + csg + cs * cs * b, T(0));
             }
             rotd = true;
           }
@@ -434,7 +426,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
     if (!rot) break;
   }
   if (lane == 0 && flops_out && (nevals | nrots))
-    atomicAdd(flops_out, 2.0 * (double)nevals * nrow + 6.0 * (double)nrots * (nrow + ncol));
+    atomicAdd(flops_out, 6.0 * (double)nevals * nrow + 6.0 * (double)nrots * (nrow + ncol));
   for (int col = warp; col < ncol; col += nw) {
     T a = 0;
     for (int q = lane; q < nrow; q += 32) a += W[(long)col * ldw + q] * W[(long)col * ldw + q];

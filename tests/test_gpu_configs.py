@@ -54,6 +54,12 @@ def test_variable_coefficient_n64_fp32_refined(acr, grf64):
     u = from_cols(x)[:, 0]
     assert iterative.rel_residual(n, g, u, f)[0] <= 1.01e-10
     assert rel(u, ref) < 1e-8
+    # the truncation actually compresses: every block rank stays well below its size
+    s = acr.acr_get_stats(h)
+    m = n * n
+    for row in s["max_rank"][: s["levels_cr"]]:
+        for lvl, k in enumerate(row):
+            assert k <= (m >> (lvl + 1)) // 2, (lvl, k, row)
 
 
 def test_helmholtz_n64_fgmres_ranks(acr):

@@ -351,8 +351,9 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
   // truncation threshold; Jacobi leaves them alone (their pairwise cosines
   // are rounding noise and would never settle).
   // Columns at the rounding-noise level (norm ~ u ||C||) have random
-  // directions; 64 u ||C||_F keeps them out as well.
-  const T tau = fmax(T(1e-4) * tol * tol, T(4096) * unit * unit);
+  // directions and are left alone too (32 u ||C||_F); the truncation below
+  // drops everything under this floor, so no unrotated column is kept.
+  const T tau = fmax(T(1e-4) * tol * tol, T(1024) * unit * unit);
   const T floor2 = tau * fro2;
   const int ne = ncol + (ncol & 1);
   long long nevals = 0, nrots = 0;  // per warp (identical on its lanes)
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
   T smax = sig[ord[0]];
   int rank = 0;
   if (smax > T(0)) {
-    T thr = fmax(tol * smax, smax * unit * T(4));
+    T thr = fmax(fmax(tol * smax, smax * unit * T(4)), sqrt(floor2));
     for (int t = 0; t < ncol; ++t) rank += sig[ord[t]] > thr;
   }
   T* X = Xall + bi * (long)r * r;

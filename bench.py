@@ -47,6 +47,22 @@ WORKLOAD = {
 METRIC = "factor+solve DOF/s at n=128 (FP32 ACR + FP64 refinement to 1e-10)"
 
 
+def reduce_step_time(ms, world, dist, device):
+    """Replicas: every rank times its own copy; the job time is the slowest rank's."""
+    if world <= 1 or dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world, N, nrhs, ms):
+    """Whole-job DOF/s: all ranks' right-hand sides over the slowest rank's step time."""
+    return world * N * nrhs / (ms * 1e-3)
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -276,11 +292,8 @@ def main():
         torch.cuda.synchronize()
     clocks = clk.summary()
     ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N * nrhs / (ms * 1e-3)
+    ms = reduce_step_time(ms, world, dist, "cuda")
+    value = aggregate_value(world, N, nrhs, ms)
 
     # end-to-end through the C ABI: host kappa and pinned host RHS, result read back every step
     e2e = None

@@ -219,9 +219,16 @@ __global__ void __launch_bounds__(kCholThreads) k_pchol(int r, const T* Gall, T 
       } else if (i == p) {
         v = sq;
       } else {
-        v = G[(long)p * r + i];
-        for (int u = 0; u < t; ++u) v -= colp[u] * R[(long)u * r + i];
-        v *= isq;
+        T v0 = G[(long)p * r + i], v1 = T(0), v2 = T(0), v3 = T(0);
+        int u = 0;
+        for (; u + 3 < t; u += 4) {  // four independent chains keep loads in flight
+          v0 -= colp[u] * R[(long)u * r + i];
+          v1 -= colp[u + 1] * R[(long)(u + 1) * r + i];
+          v2 -= colp[u + 2] * R[(long)(u + 2) * r + i];
+          v3 -= colp[u + 3] * R[(long)(u + 3) * r + i];
+        }
+        for (; u < t; ++u) v0 -= colp[u] * R[(long)u * r + i];
+        v = ((v0 + v1) + (v2 + v3)) * isq;
       }
       R[(long)t * r + i] = v;
       if (i == p) d[i] = T(-1);
@@ -471,7 +478,9 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
 template <class T>
 __global__ void __launch_bounds__(256) k_coef(int r, int Kout, long NB, int qr, const T* Rall, const int* pivall,
                                               const int* kkall, const T* Xall, const T* Yall, const T* sigall,
-                                              const int* rankall, const T* scall, T* Zall) {
+                                              const int* rankall, const T* scall, T* Zall, int smem_tri) {
+  extern __shared__ unsigned char smraw[];
+  T* tri = reinterpret_cast<T*>(smraw);  // packed upper triangle of R11 (row u: entries v >= u)
   const long j = blockIdx.x;
   const int side = (int)(j / NB);
   const long bi = j % NB;
@@ -483,11 +492,26 @@ __global__ void __launch_bounds__(256) k_coef(int r, int Kout, long NB, int qr, 
   const int rank = rankall[bi];
   T* Z = Zall + j * (long)r * Kout;
   for (long e = threadIdx.x; e < (long)r * Kout; e += blockDim.x) Z[e] = T(0);
+  const bool staged = !qr && (long)k * (k + 1) / 2 <= smem_tri;
+  if (staged) {
+    // row u starts at u*k - u*(u-1)/2; entry (u, v) at start + (v - u)
+    for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) {
+      int u = (int)(e / k), v = (int)(e % k);
+      if (v >= u) tri[(long)u * k - (long)u * (u - 1) / 2 + (v - u)] = R[(long)u * r + piv[v]];
+    }
+  }
   __syncthreads();
   for (int t = threadIdx.x; t < rank; t += blockDim.x) {
     const T sq = sqrt(sig[t]);
     if (qr) {
       for (int u = 0; u < k; ++u) Z[(long)u * Kout + t] = XY[(long)u * r + t] * sq;
+    } else if (staged) {
+      for (int u = k - 1; u >= 0; --u) {
+        const T* row = tri + (long)u * k - (long)u * (u - 1) / 2;
+        T v = XY[(long)u * r + t] * sq;
+        for (int w = u + 1; w < k; ++w) v -= row[w - u] * Z[(long)piv[w] * Kout + t];
+        Z[(long)piv[u] * Kout + t] = v / row[0];
+      }
     } else {
       for (int u = k - 1; u >= 0; --u) {
         T v = XY[(long)u * r + t] * sq;
@@ -602,8 +626,15 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
   }
   DBuf<T> Z(c, 2 * NB * (size_t)r * Kout);
   c.kbegin();
-  k_coef<T><<<(unsigned)(2 * NB), 256, 0, c.st>>>(r, Kout, NB, qr ? 1 : 0, R.p, piv.p, kk.p, Xo.p, Yo.p, sig.p,
-                                                 rank.p, scale.p, Z.p);
+  {
+    const size_t cap = 200 * 1024;
+    const long need = qr ? 0 : (long)r * (r + 1) / 2;
+    const int smem_tri = (int)std::min<long>(need, (long)(cap / sizeof(T)));
+    const size_t sm = (size_t)smem_tri * sizeof(T);
+    if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_coef<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_coef<T><<<(unsigned)(2 * NB), 256, sm, c.st>>>(r, Kout, NB, qr ? 1 : 0, R.p, piv.p, kk.p, Xo.p, Yo.p, sig.p,
+                                                    rank.p, scale.p, Z.p, smem_tri);
+  }
   c.kend(KC_COEF, 0, 2.0 * NB * sizeof(T) * ((double)r * r + (double)r * Kout));
   Uout = DBuf<T>(c, (size_t)P * m * Kout);
   Vout = DBuf<T>(c, (size_t)P * m * Kout);

@@ -67,6 +67,9 @@ typedef struct {
   int inverse_fp64;       /* ACR_FP32 only: 1 = leaf and Woodbury-coupling inverses computed in FP64 */
   int tensor_cores;       /* ACR_FP32 only: 1 = large GEMM tiles on the tensor pipe with a 3xTF32 split
                              (FP32-level accuracy) instead of FP32 FMA */
+  int core_svd;           /* truncation of the recompression core: 0 = auto (rank-revealing QR with column
+                             pivoting for ACR_FP32, one-sided Jacobi SVD for ACR_FP64), 1 = Jacobi SVD,
+                             2 = pivoted QR */
   int coarse_dense_max;   /* coarsest plane factorised densely in FP64 when n^2 <= this (0 = default 4096,
                              negative = never; otherwise it is inverted as a HODLR matrix) */
   int graphs;             /* 1 = capture the solve sweeps once per (nrhs, transpose) as a CUDA graph and replay
@@ -86,7 +89,7 @@ typedef struct {
   long long gemm_flops;                   /* algorithmic GEMM flops issued by the factorisation */
   long long kernel_launches;              /* kernels launched by the last call */
   /* Per kernel class, accumulated over the handle's life (times only with opts.profile = 1):
-   * 0 batched GEMM, 1 split-K reduction, 2 Householder QR, 3 pivoted Cholesky, 4 Jacobi SVD,
+   * 0 batched GEMM, 1 split-K reduction, 2 Householder QR, 3 pivoted Cholesky, 4 core truncation (Jacobi SVD or pivoted QR),
    * 5 rebuild coefficients, 6 Gauss-Jordan inverse, 7 copies/fills, 8 assembly, 9 RHS permutation,
    * 10 FP64 stencil and column reductions.  flops/bytes are algorithmic counts (each operand once). */
   double kc_ms[16];

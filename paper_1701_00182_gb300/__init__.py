@@ -30,7 +30,7 @@ ACR_ERR_CUDA = 5
 ACR_ERR_NOT_CONVERGED = 6
 ACR_FP64 = 0
 ACR_FP32 = 1
-KERNEL_CLASSES = ("gemm", "splitk_reduce", "householder_qr", "pivoted_cholesky", "jacobi_svd", "rebuild_coef",
+KERNEL_CLASSES = ("gemm", "splitk_reduce", "householder_qr", "pivoted_cholesky", "core_truncation", "rebuild_coef",
                   "gauss_jordan", "copy", "assemble", "permute", "stencil_fp64")
 
 
@@ -46,6 +46,7 @@ class AcrOpts(C.Structure):
         ("profile", C.c_int),
         ("inverse_fp64", C.c_int),
         ("tensor_cores", C.c_int),
+        ("core_svd", C.c_int),
         ("coarse_dense_max", C.c_int),
         ("graphs", C.c_int),
     ]

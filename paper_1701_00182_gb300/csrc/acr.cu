@@ -676,6 +676,7 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     c.profile = o.profile != 0;
     c.inverse_fp64 = o.inverse_fp64 != 0;
     c.tensor = o.tensor_cores != 0;
+    c.core_svd = o.core_svd;
     ACR_CUDA(cudaMalloc(&c.d_flag, 4 * sizeof(int)));
     ACR_CUDA(cudaMemsetAsync(c.d_flag, 0, 4 * sizeof(int), c.st));
     ACR_CUDA(cudaMalloc(&c.d_jflops, sizeof(double)));

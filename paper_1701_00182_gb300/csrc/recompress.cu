@@ -471,6 +471,177 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
   if (tid == 0) rankall[bi] = rank;
 }
 
+// ---- rank-revealing QR (column pivoting) of the core ---------------------------
+// C Pi = Q R (Householder, columns chosen by largest remaining norm), stopped
+// when the largest remaining column norm is <= tol * (largest initial column
+// norm).  Output in the same form as the Jacobi SVD: C ~ X diag(sig) Y^T with
+// X = Q_k (kL x k, orthonormal), sig_t = |R_tt|, Y[Pi(j)][t] = R[t][j] / sig_t.
+constexpr int kQrcpThreads = 1024;
+template <class T>
+__global__ void __launch_bounds__(kQrcpThreads) k_qrcp(int r, const T* Call, const int* kk, long NB, T* Wall,
+                                                       T* Xall, T* Yall, T* sigall, int* rankall, T tol,
+                                                       int smem_elems, double* flops_out) {
+  extern __shared__ unsigned char smraw[];
+  T* nrm = reinterpret_cast<T*>(smraw);
+  T* nrm0 = nrm + r;
+  T* tau = nrm0 + r;
+  int* perm = reinterpret_cast<int*>(tau + r);
+  T* Ws = reinterpret_cast<T*>(perm + r + (r & 1));
+  __shared__ T wv[32];
+  __shared__ int wi[32];
+  __shared__ T s_thr2;
+  __shared__ int s_p, s_stop;
+  const long bi = blockIdx.x;
+  const T* C = Call + bi * (long)r * r;
+  const int kL = kk[bi], kR = kk[NB + bi];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const bool insm = (long)kL * kR <= smem_elems;
+  const long ldw = insm ? kL : r;
+  T* W = insm ? Ws : Wall + bi * (long)r * r;  // column major kL x kR
+  T* X = Xall + bi * (long)r * r;
+  T* Y = Yall + bi * (long)r * r;
+  const int kmax = min(kL, kR);
+  if (kmax == 0) {
+    if (tid == 0) rankall[bi] = 0;
+    for (int i = tid; i < r; i += blockDim.x) sigall[bi * r + i] = T(0);
+    return;
+  }
+  for (long e = tid; e < (long)kL * kR; e += blockDim.x) {
+    int row = (int)(e % kL), col = (int)(e / kL);
+    W[(long)col * ldw + row] = C[(long)row * r + col];
+  }
+  __syncthreads();
+  for (int col = warp; col < kR; col += nw) {
+    T a = 0;
+    for (int q = lane; q < kL; q += 32) a += W[(long)col * ldw + q] * W[(long)col * ldw + q];
+    a = warp_sum(a);
+    if (lane == 0) { nrm[col] = a; nrm0[col] = a; perm[col] = col; }
+  }
+  __syncthreads();
+  int rank = 0;
+  for (int st = 0; st < kmax; ++st) {
+    // pivot: largest remaining column norm
+    T best = T(-1);
+    int bi2 = 0x7fffffff;
+    for (int j = st + tid; j < kR; j += blockDim.x)
+      if (nrm[j] > best) { best = nrm[j]; bi2 = j; }
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi2, o);
+      if (ov > best || (ov == best && oi < bi2)) { best = ov; bi2 = oi; }
+    }
+    if (lane == 0) { wv[warp] = best; wi[warp] = bi2; }
+    __syncthreads();
+    if (tid == 0) {
+      T b = T(-1);
+      int bb = st;
+      for (int w = 0; w < nw; ++w)
+        if (wv[w] > b || (wv[w] == b && wi[w] < bb)) { b = wv[w]; bb = wi[w]; }
+      if (st == 0) s_thr2 = tol * tol * b;
+      s_p = bb;
+      s_stop = !(b > s_thr2) || !(b > T(0));
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_p;
+    if (p != st) {
+      for (int q = tid; q < kL; q += blockDim.x) {
+        T t = W[(long)st * ldw + q];
+        W[(long)st * ldw + q] = W[(long)p * ldw + q];
+        W[(long)p * ldw + q] = t;
+      }
+      if (tid == 0) {
+        T t = nrm[st]; nrm[st] = nrm[p]; nrm[p] = t;
+        t = nrm0[st]; nrm0[st] = nrm0[p]; nrm0[p] = t;
+        int ti = perm[st]; perm[st] = perm[p]; perm[p] = ti;
+      }
+    }
+    __syncthreads();
+    // Householder reflector of column st, rows st..kL-1
+    T part = T(0);
+    for (int q = st + 1 + tid; q < kL; q += blockDim.x) part += W[(long)st * ldw + q] * W[(long)st * ldw + q];
+    T xn2 = block_sum(part, wv);
+    T x0 = W[(long)st * ldw + st];
+    T t = T(0), beta = x0, scal = T(0);
+    if (xn2 > T(0)) {
+      beta = -copysign(sqrt(x0 * x0 + xn2), x0);
+      t = (beta - x0) / beta;
+      scal = T(1) / (x0 - beta);
+    }
+    __syncthreads();
+    for (int q = st + 1 + tid; q < kL; q += blockDim.x) W[(long)st * ldw + q] *= scal;
+    if (tid == 0) { tau[st] = t; W[(long)st * ldw + st] = beta; }
+    __syncthreads();
+    for (int j = st + 1 + warp; j < kR; j += nw) {
+      T w = T(0);
+      if (t != T(0)) {
+        w = (lane == 0) ? W[(long)j * ldw + st] : T(0);
+        for (int q = st + 1 + lane; q < kL; q += 32) w += W[(long)st * ldw + q] * W[(long)j * ldw + q];
+        w = warp_sum(w) * t;
+        for (int q = st + 1 + lane; q < kL; q += 32) W[(long)j * ldw + q] -= w * W[(long)st * ldw + q];
+      }
+      if (lane == 0) {
+        T rsj = W[(long)j * ldw + st] - w;
+        W[(long)j * ldw + st] = rsj;
+        T nn = nrm[j] - rsj * rsj;
+        nrm[j] = nn;
+      }
+      __syncwarp();
+      // norm downdate lost its digits: recompute from the remaining rows
+      if (nrm[j] < T(0.05) * nrm0[j]) {
+        T a = 0;
+        for (int q = st + 1 + lane; q < kL; q += 32) a += W[(long)j * ldw + q] * W[(long)j * ldw + q];
+        a = warp_sum(a);
+        if (lane == 0) { nrm[j] = a; nrm0[j] = a; }
+      }
+    }
+    __syncthreads();
+    rank = st + 1;
+  }
+  // Y and sig from R (rows < rank), before Q overwrites the reflectors.
+  for (long e = tid; e < (long)rank * kR; e += blockDim.x) {
+    int tt = (int)(e / kR), j = (int)(e % kR);
+    T d = fabs(W[(long)tt * ldw + tt]);
+    T v = (j >= tt) ? W[(long)j * ldw + tt] : T(0);
+    Y[(long)perm[j] * r + tt] = d > T(0) ? v / d : T(0);
+  }
+  for (int i = tid; i < r; i += blockDim.x) sigall[bi * r + i] = (i < rank) ? fabs(W[(long)i * ldw + i]) : T(0);
+  __syncthreads();
+  // Q_k = H_0 ... H_{k-1} [I; 0] in place (backward accumulation).
+  for (int q = rank - 1; q >= 0; --q) {
+    const T tq = tau[q];
+    if (q < rank - 1) {
+      if (tid == 0) W[(long)q * ldw + q] = T(1);
+      __syncthreads();
+      for (int j = q + 1 + warp; j < rank; j += nw) {
+        T w = T(0);
+        for (int i = q + lane; i < kL; i += 32) w += W[(long)q * ldw + i] * W[(long)j * ldw + i];
+        w = warp_sum(w) * tq;
+        for (int i = q + lane; i < kL; i += 32) W[(long)j * ldw + i] -= w * W[(long)q * ldw + i];
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < kL; i += blockDim.x) {
+      if (i > q) W[(long)q * ldw + i] *= -tq;
+      else if (i < q) W[(long)q * ldw + i] = T(0);
+    }
+    if (tid == 0) W[(long)q * ldw + q] = T(1) - tq;
+    __syncthreads();
+  }
+  for (long e = tid; e < (long)rank * r; e += blockDim.x) {
+    int tt = (int)(e / r), i = (int)(e % r);
+    X[(long)i * r + tt] = (i < kL) ? W[(long)tt * ldw + i] : T(0);
+  }
+  if (tid == 0) {
+    rankall[bi] = rank;
+    if (flops_out) {  // reflector applications of the factorisation and of forming Q_k
+      double f = 0;
+      for (int q = 0; q < rank; ++q) f += 4.0 * (kL - q) * ((kR - q - 1) + (rank - q - 1));
+      atomicAdd(flops_out, f);
+    }
+  }
+}
+
 // ---- coefficients of the rebuild ---------------------------------------------
 // Z (r x Kout, row major) per side of block bi such that the new factor is
 // factor * Z:  QR path  Z[0:k, t] = X[:, t] sqrt(s_t);  Gram path  Z[piv[u], t] = z[u],
@@ -609,10 +780,23 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     int smem_elems = (int)std::min<size_t>((size_t)r * r, cap > base ? (cap - base) / sizeof(T) : 0);
     size_t sm = base + (size_t)smem_elems * sizeof(T);
     ACR_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    c.kbegin();
-    k_jacobi<T><<<(unsigned)NB, kJacThreads, sm, c.st>>>(r, Cc.p, kk.p, NB, W.p, Vw.p, Xo.p, Yo.p, sig.p, rank.p,
-                                                         T(tol), 24, smem_elems, c.d_flag + 1, c.d_jflops);
-    c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r);
+    const bool use_qrcp = c.core_svd == 2 || (c.core_svd == 0 && sizeof(T) == 4);
+    if (use_qrcp) {
+      size_t base2 = (size_t)r * (3 * sizeof(T) + sizeof(int)) + ((r & 1) ? sizeof(int) : 0);
+      base2 = (base2 + 15) / 16 * 16;
+      int se2 = (int)std::min<size_t>((size_t)r * r, cap > base2 ? (cap - base2) / sizeof(T) : 0);
+      size_t sm2 = base2 + (size_t)se2 * sizeof(T);
+      ACR_CUDA(cudaFuncSetAttribute(k_qrcp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+      c.kbegin();
+      k_qrcp<T><<<(unsigned)NB, kQrcpThreads, sm2, c.st>>>(r, Cc.p, kk.p, NB, W.p, Xo.p, Yo.p, sig.p, rank.p, T(tol),
+                                                           se2, c.d_jflops);
+      c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r);
+    } else {
+      c.kbegin();
+      k_jacobi<T><<<(unsigned)NB, kJacThreads, sm, c.st>>>(r, Cc.p, kk.p, NB, W.p, Vw.p, Xo.p, Yo.p, sig.p, rank.p,
+                                                           T(tol), 24, smem_elems, c.d_flag + 1, c.d_jflops);
+      c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r);
+    }
   }
   std::vector<int> hr(NB);
   ACR_CUDA(cudaMemcpyAsync(hr.data(), rank.p, NB * sizeof(int), cudaMemcpyDeviceToHost, c.st));

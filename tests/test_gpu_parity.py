@@ -225,3 +225,16 @@ def test_coarsest_plane_dense_fp64_and_hodlr(acr, coarse_dense_max, dense):
     assert rel(acr.acr_get_factor_block(h, 5, 0, 0), np.linalg.inv(fac.coarse_D)) < 1e-12
     f = synthetic.uniform_rhs(n, 3)
     assert rel(_solve(acr, h, f), direct.dense_solve(n, g, f)) < 1e-12
+
+
+@pytest.mark.parametrize("core_svd", [1, 2])
+def test_core_truncation_jacobi_and_pivoted_qr(acr, core_svd):
+    """Both truncations of the recompression core (Jacobi SVD, pivoted QR) give
+    a FP64 direct solve within the accuracy bar, and compress the blocks."""
+    n = 16
+    g = synthetic.gaussian_random_field(n, 1)
+    f = synthetic.uniform_rhs(n, 0)
+    h = acr.acr_factor(n, g, 1e-6, 16, core_svd=core_svd)
+    assert rel(_solve(acr, h, f), direct.dense_solve(n, g, f)) < 1e-5
+    s = acr.acr_get_stats(h)
+    assert max(s["max_rank"][1]) < 64

@@ -114,6 +114,25 @@ void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A,
 template <class T>
 void gemm_sym(Ctx& c, int M, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta, Op<T> C);
 
+// Fused HODLR x panel expansion (leaf product + every level's expansion).
+template <class T>
+struct HexpArgs {
+  int m = 0, b = 0, w = 0, nl = 0, leaf_trans = 0;
+  const T* leaf = nullptr;
+  long lps = 0;
+  const T* W = nullptr;
+  long wld = 0, wps = 0;
+  T* Y = nullptr;
+  long yld = 0, yps = 0;
+  T alpha = T(1), beta = T(0);
+  const T* U[MAXL] = {};
+  long ups[MAXL] = {};
+  const T* C[MAXL] = {};
+  int K[MAXL] = {}, s[MAXL] = {}, nclus[MAXL] = {};
+};
+template <class T>
+void hexpand(Ctx& c, const HexpArgs<T>& a, int P);
+
 // Panel view: rows m per plane, element (row, col) at p[plane*ps + row*ld + col].
 template <class T>
 struct Pan {

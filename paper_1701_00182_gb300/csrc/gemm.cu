@@ -616,6 +616,114 @@ void gemm_sym(Ctx& c, int M, int K, int nplanes, int nclus, T alpha, Op<T> A, Op
   gemm_impl<T>(c, M, M, K, nplanes, nclus, alpha, A, B, beta, C, 1);
 }
 
+// ---- fused multi-level expansion of a HODLR x panel product -------------------
+// Y[rows of leaf] = alpha * ( leaf * W[rows]  +  sum_l U_l[rows] * C_l[sibling of the
+// row's level-(l+1) cluster] ) + beta * Y[rows]:  the leaf product and every
+// level's expansion in one pass over an inner dimension b + sum_l K_l, so Y is
+// read and written once.  One CTA per (plane, leaf, 64 output columns).
+template <class T>
+__global__ void __launch_bounds__(256) k_hexpand(HexpArgs<T> a) {
+  constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+  __shared__ T As[BK][BM + 4];
+  __shared__ T Bs[BK][BN + 4];
+  const int nleaf = a.m / a.b;
+  const int plane = blockIdx.x / nleaf, lf = blockIdx.x % nleaf;
+  const int n0 = blockIdx.y * BN;
+  const int row0 = lf * a.b;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  // segment -1: leaf; segments 0..nl-1: levels
+  for (int sg = -1; sg < a.nl; ++sg) {
+    const T* Ap;
+    long ars, acs;
+    const T* Bp;
+    long brs;
+    int K;
+    if (sg < 0) {
+      const T* lfp = a.leaf + plane * a.lps + (long)lf * a.b * a.b;
+      Ap = lfp;
+      ars = a.leaf_trans ? 1 : a.b;
+      acs = a.leaf_trans ? a.b : 1;
+      Bp = a.W + plane * a.wps + (long)row0 * a.wld;
+      brs = a.wld;
+      K = a.b;
+    } else {
+      K = a.K[sg];
+      const int s = a.s[sg];
+      const int c = row0 / s;
+      Ap = a.U[sg] + plane * a.ups[sg] + (long)row0 * K;
+      ars = K;
+      acs = 1;
+      Bp = a.C[sg] + ((long)plane * a.nclus[sg] + (c ^ 1)) * (long)K * a.w;
+      brs = a.w;
+    }
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      for (int e = tid; e < BM * BK; e += 256) {
+        int ii, kk;
+        if (acs == 1) { ii = e / BK; kk = e % BK; } else { ii = e % BM; kk = e / BM; }
+        int gk = k0 + kk;
+        As[kk][ii] = (ii < a.b && gk < K) ? Ap[(long)ii * ars + (long)gk * acs] : T(0);
+      }
+      for (int e = tid; e < BK * BN; e += 256) {
+        int kk = e / BN, jj = e % BN;
+        int gk = k0 + kk, gj = n0 + jj;
+        Bs[kk][jj] = (gk < K && gj < a.w) ? Bp[(long)gk * brs + gj] : T(0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T av[TM], bv[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) av[i] = As[kk][ty * TM + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+  T* Yp = a.Y + plane * a.yps + (long)row0 * a.yld;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int r = ty * TM + i;
+    if (r >= a.b) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int cj = n0 + tx * TN + j;
+      if (cj >= a.w) continue;
+      T* yp = Yp + (long)r * a.yld + cj;
+      T v = a.alpha * acc[i][j];
+      if (a.beta != T(0)) v += a.beta * *yp;
+      *yp = v;
+    }
+  }
+}
+
+template <class T>
+void hexpand(Ctx& c, const HexpArgs<T>& a, int P) {
+  if (P <= 0 || a.w <= 0) return;
+  if (a.b > 64) throw AcrError(1, "fused expansion supports leaves of at most 64 rows");
+  dim3 grid((unsigned)((long)P * (a.m / a.b)), (a.w + 63) / 64);
+  double fl = 2.0 * a.b * a.b, by = 0;
+  for (int l = 0; l < a.nl; ++l) fl += 2.0 * a.b * a.K[l];
+  fl *= (double)P * (a.m / a.b) * a.w;
+  by = (double)sizeof(T) * P * a.m * (a.b + 2.0 * a.w);
+  for (int l = 0; l < a.nl; ++l) by += (double)sizeof(T) * P * a.m * a.K[l];
+  c.kbegin();
+  k_hexpand<T><<<grid, 256, 0, c.st>>>(a);
+  c.kend(KC_GEMM, fl, by);
+  c.gemm_flops += (long long)fl;
+}
+template void hexpand<float>(Ctx&, const HexpArgs<float>&, int);
+template void hexpand<double>(Ctx&, const HexpArgs<double>&, int);
+
 template void gemm_sym<float>(Ctx&, int, int, int, int, float, Op<float>, Op<float>, float, Op<float>);
 template void gemm_sym<double>(Ctx&, int, int, int, int, double, Op<double>, Op<double>, double, Op<double>);
 template void gemm<float>(Ctx&, int, int, int, int, int, float, Op<float>, Op<float>, float, Op<float>);

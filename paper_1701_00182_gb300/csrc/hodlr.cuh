@@ -39,28 +39,55 @@ void axpy2d(Ctx& c, int P, long rows, int cols, T alpha, const T* src, long sld,
             long dps);
 
 // Y = alpha * M^_{>=lmin} W + beta * Y  (trans: M^T).  W, Y: m x w per plane.
+// Coefficients c = V|c^T W|c per level (batched reductions), then one fused
+// expansion of the leaf product and all levels.
 template <class T>
 void hmatvec(Ctx& c, const HMat<T>& A, int lmin, bool trans, Pan<T> W, Pan<T> Y, int w, T alpha, T beta) {
   const int P = A.P, m = A.m, b = A.b, nleaf = m / b;
   if (P <= 0 || w <= 0) return;
-  c.tag = "mv_leaf";
-  gemm<T>(c, b, w, b, P, nleaf, alpha, opm<T>(A.leaf, trans ? 1 : b, trans ? b : 1, A.lps, (long)b * b),
-          opm<T>(W.p, W.ld, 1, W.ps, (long)b * W.ld), beta, opm<T>(Y.p, Y.ld, 1, Y.ps, (long)b * Y.ld));
+  if (b > 64) {
+    c.tag = "mv_leaf";
+    gemm<T>(c, b, w, b, P, nleaf, alpha, opm<T>(A.leaf, trans ? 1 : b, trans ? b : 1, A.lps, (long)b * b),
+            opm<T>(W.p, W.ld, 1, W.ps, (long)b * W.ld), beta, opm<T>(Y.p, Y.ld, 1, Y.ps, (long)b * Y.ld));
+    for (int l = std::max(lmin, 0); l < A.L; ++l) {
+      const int K = A.K[l];
+      if (K == 0) continue;
+      const int s = m >> (l + 1), nclus = 1 << (l + 1);
+      T* Cf = trans ? A.U[l] : A.V[l];
+      T* Ex = trans ? A.V[l] : A.U[l];
+      DBuf<T> cb(c, (size_t)P * nclus * K * w);
+      c.tag = "mv_coef";
+      gemm<T>(c, K, w, s, P, nclus, T(1), opm<T>(Cf, 1, K, A.pps[l], (long)s * K),
+              opm<T>(W.p, W.ld, 1, W.ps, (long)s * W.ld), T(0), opm<T>(cb.p, w, 1, (long)nclus * K * w, (long)K * w));
+      c.tag = "mv_expand";
+      gemm<T>(c, s, w, K, P, nclus, alpha, opm<T>(Ex, K, 1, A.pps[l], (long)s * K),
+              opm<T>(cb.p, w, 1, (long)nclus * K * w, (long)K * w, 1), T(1),
+              opm<T>(Y.p, Y.ld, 1, Y.ps, (long)s * Y.ld));
+    }
+    return;
+  }
+  HexpArgs<T> ha;
+  ha.m = m; ha.b = b; ha.w = w; ha.leaf_trans = trans ? 1 : 0;
+  ha.leaf = A.leaf; ha.lps = A.lps;
+  ha.W = W.p; ha.wld = W.ld; ha.wps = W.ps;
+  ha.Y = Y.p; ha.yld = Y.ld; ha.yps = Y.ps;
+  ha.alpha = alpha; ha.beta = beta;
+  DBuf<T> cbs[MAXL];
   for (int l = std::max(lmin, 0); l < A.L; ++l) {
     const int K = A.K[l];
     if (K == 0) continue;
     const int s = m >> (l + 1), nclus = 1 << (l + 1);
     T* Cf = trans ? A.U[l] : A.V[l];
     T* Ex = trans ? A.V[l] : A.U[l];
-    DBuf<T> cb(c, (size_t)P * nclus * K * w);
+    cbs[l] = DBuf<T>(c, (size_t)P * nclus * K * w);
     c.tag = "mv_coef";
     gemm<T>(c, K, w, s, P, nclus, T(1), opm<T>(Cf, 1, K, A.pps[l], (long)s * K),
-            opm<T>(W.p, W.ld, 1, W.ps, (long)s * W.ld), T(0), opm<T>(cb.p, w, 1, (long)nclus * K * w, (long)K * w));
-    c.tag = "mv_expand";
-    gemm<T>(c, s, w, K, P, nclus, alpha, opm<T>(Ex, K, 1, A.pps[l], (long)s * K),
-            opm<T>(cb.p, w, 1, (long)nclus * K * w, (long)K * w, 1), T(1),
-            opm<T>(Y.p, Y.ld, 1, Y.ps, (long)s * Y.ld));
+            opm<T>(W.p, W.ld, 1, W.ps, (long)s * W.ld), T(0), opm<T>(cbs[l].p, w, 1, (long)nclus * K * w, (long)K * w));
+    const int i = ha.nl++;
+    ha.U[i] = Ex; ha.ups[i] = A.pps[l]; ha.C[i] = cbs[l].p; ha.K[i] = K; ha.s[i] = s; ha.nclus[i] = nclus;
   }
+  c.tag = "mv_expand";
+  hexpand<T>(c, ha, P);
 }
 
 // Sum (Woodbury) form of the inverse of P HODLR matrices.

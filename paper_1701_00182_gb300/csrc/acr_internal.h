@@ -129,6 +129,7 @@ struct HexpArgs {
   long ups[MAXL] = {};
   const T* C[MAXL] = {};
   int K[MAXL] = {}, s[MAXL] = {}, nclus[MAXL] = {};
+  int ncol[MAXL] = {};  // level applies to the first ncol columns; its coefficient rows have stride ncol
 };
 template <class T>
 void hexpand(Ctx& c, const HexpArgs<T>& a, int P);

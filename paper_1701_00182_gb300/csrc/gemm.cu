@@ -618,7 +618,8 @@ void gemm_sym(Ctx& c, int M, int K, int nplanes, int nclus, T alpha, Op<T> A, Op
 
 // ---- fused multi-level expansion of a HODLR x panel product -------------------
 // Y[rows of leaf] = alpha * ( leaf * W[rows]  +  sum_l U_l[rows] * C_l[sibling of the
-// row's level-(l+1) cluster] ) + beta * Y[rows]:  the leaf product and every
+// row's level-(l+1) cluster] ) + beta * Y[rows], where level l only reaches the
+// first ncol_l columns:  the leaf product and every
 // level's expansion in one pass over an inner dimension b + sum_l K_l, so Y is
 // read and written once.  One CTA per (plane, leaf, 64 output columns).
 template <class T>
@@ -642,7 +643,7 @@ __global__ void __launch_bounds__(256) k_hexpand(HexpArgs<T> a) {
     long ars, acs;
     const T* Bp;
     long brs;
-    int K;
+    int K, nlim = a.w;
     if (sg < 0) {
       const T* lfp = a.leaf + plane * a.lps + (long)lf * a.b * a.b;
       Ap = lfp;
@@ -653,13 +654,15 @@ __global__ void __launch_bounds__(256) k_hexpand(HexpArgs<T> a) {
       K = a.b;
     } else {
       K = a.K[sg];
+      nlim = a.ncol[sg];
+      if (n0 >= nlim) continue;  // uniform over the CTA
       const int s = a.s[sg];
       const int c = row0 / s;
       Ap = a.U[sg] + plane * a.ups[sg] + (long)row0 * K;
       ars = K;
       acs = 1;
-      Bp = a.C[sg] + ((long)plane * a.nclus[sg] + (c ^ 1)) * (long)K * a.w;
-      brs = a.w;
+      Bp = a.C[sg] + ((long)plane * a.nclus[sg] + (c ^ 1)) * (long)K * nlim;
+      brs = nlim;
     }
     for (int k0 = 0; k0 < K; k0 += BK) {
       for (int e = tid; e < BM * BK; e += 256) {
@@ -671,7 +674,7 @@ __global__ void __launch_bounds__(256) k_hexpand(HexpArgs<T> a) {
       for (int e = tid; e < BK * BN; e += 256) {
         int kk = e / BN, jj = e % BN;
         int gk = k0 + kk, gj = n0 + jj;
-        Bs[kk][jj] = (gk < K && gj < a.w) ? Bp[(long)gk * brs + gj] : T(0);
+        Bs[kk][jj] = (gk < K && gj < nlim) ? Bp[(long)gk * brs + gj] : T(0);
       }
       __syncthreads();
 #pragma unroll
@@ -711,9 +714,9 @@ void hexpand(Ctx& c, const HexpArgs<T>& a, int P) {
   if (P <= 0 || a.w <= 0) return;
   if (a.b > 64) throw AcrError(1, "fused expansion supports leaves of at most 64 rows");
   dim3 grid((unsigned)((long)P * (a.m / a.b)), (a.w + 63) / 64);
-  double fl = 2.0 * a.b * a.b, by = 0;
-  for (int l = 0; l < a.nl; ++l) fl += 2.0 * a.b * a.K[l];
-  fl *= (double)P * (a.m / a.b) * a.w;
+  double fl = 2.0 * a.b, by = 0;  // per output element
+  for (int l = 0; l < a.nl; ++l) fl += 2.0 * a.K[l] * ((double)a.ncol[l] / a.w);
+  fl *= (double)P * a.m * a.w;
   by = (double)sizeof(T) * P * a.m * (a.b + 2.0 * a.w);
   for (int l = 0; l < a.nl; ++l) by += (double)sizeof(T) * P * a.m * a.K[l];
   c.kbegin();

@@ -38,30 +38,39 @@ template <class T>
 void axpy2d(Ctx& c, int P, long rows, int cols, T alpha, const T* src, long sld, long sps, T* dst, long dld,
             long dps);
 
-// Y = alpha * M^_{>=lmin} W + beta * Y  (trans: M^T).  W, Y: m x w per plane.
-// Coefficients c = V|c^T W|c per level (batched reductions), then one fused
-// expansion of the leaf product and all levels.
+// Y = alpha * (leaf part + sum_l [level l of M restricted to the first ncol[l]
+// columns of W]) + beta * Y   (trans: M^T).  W, Y: m x w per plane.
+// Coefficients c_l = V_l|c^T W|c[:, :ncol[l]] per level (batched reductions),
+// then one fused expansion of the leaf product and all levels.  A level with
+// ncol[l] = 0 is skipped; the plain product is ncol[l] = w for every level.
 template <class T>
-void hmatvec(Ctx& c, const HMat<T>& A, int lmin, bool trans, Pan<T> W, Pan<T> Y, int w, T alpha, T beta) {
+void hmatvec_cols(Ctx& c, const HMat<T>& A, bool trans, Pan<T> W, Pan<T> Y, int w, const int* ncol, T alpha,
+                  T beta) {
   const int P = A.P, m = A.m, b = A.b, nleaf = m / b;
   if (P <= 0 || w <= 0) return;
+  DBuf<T> cbs[MAXL];
+  for (int l = 0; l < A.L; ++l) {
+    const int K = A.K[l], nc = ncol[l];
+    if (K == 0 || nc == 0) continue;
+    const int s = m >> (l + 1), nclus = 1 << (l + 1);
+    T* Cf = trans ? A.U[l] : A.V[l];
+    cbs[l] = DBuf<T>(c, (size_t)P * nclus * K * nc);
+    c.tag = "mv_coef";
+    gemm<T>(c, K, nc, s, P, nclus, T(1), opm<T>(Cf, 1, K, A.pps[l], (long)s * K),
+            opm<T>(W.p, W.ld, 1, W.ps, (long)s * W.ld), T(0), opm<T>(cbs[l].p, nc, 1, (long)nclus * K * nc, (long)K * nc));
+  }
   if (b > 64) {
     c.tag = "mv_leaf";
     gemm<T>(c, b, w, b, P, nleaf, alpha, opm<T>(A.leaf, trans ? 1 : b, trans ? b : 1, A.lps, (long)b * b),
             opm<T>(W.p, W.ld, 1, W.ps, (long)b * W.ld), beta, opm<T>(Y.p, Y.ld, 1, Y.ps, (long)b * Y.ld));
-    for (int l = std::max(lmin, 0); l < A.L; ++l) {
-      const int K = A.K[l];
-      if (K == 0) continue;
+    for (int l = 0; l < A.L; ++l) {
+      const int K = A.K[l], nc = ncol[l];
+      if (K == 0 || nc == 0) continue;
       const int s = m >> (l + 1), nclus = 1 << (l + 1);
-      T* Cf = trans ? A.U[l] : A.V[l];
       T* Ex = trans ? A.V[l] : A.U[l];
-      DBuf<T> cb(c, (size_t)P * nclus * K * w);
-      c.tag = "mv_coef";
-      gemm<T>(c, K, w, s, P, nclus, T(1), opm<T>(Cf, 1, K, A.pps[l], (long)s * K),
-              opm<T>(W.p, W.ld, 1, W.ps, (long)s * W.ld), T(0), opm<T>(cb.p, w, 1, (long)nclus * K * w, (long)K * w));
       c.tag = "mv_expand";
-      gemm<T>(c, s, w, K, P, nclus, alpha, opm<T>(Ex, K, 1, A.pps[l], (long)s * K),
-              opm<T>(cb.p, w, 1, (long)nclus * K * w, (long)K * w, 1), T(1),
+      gemm<T>(c, s, nc, K, P, nclus, alpha, opm<T>(Ex, K, 1, A.pps[l], (long)s * K),
+              opm<T>(cbs[l].p, nc, 1, (long)nclus * K * nc, (long)K * nc, 1), T(1),
               opm<T>(Y.p, Y.ld, 1, Y.ps, (long)s * Y.ld));
     }
     return;
@@ -72,22 +81,24 @@ void hmatvec(Ctx& c, const HMat<T>& A, int lmin, bool trans, Pan<T> W, Pan<T> Y,
   ha.W = W.p; ha.wld = W.ld; ha.wps = W.ps;
   ha.Y = Y.p; ha.yld = Y.ld; ha.yps = Y.ps;
   ha.alpha = alpha; ha.beta = beta;
-  DBuf<T> cbs[MAXL];
-  for (int l = std::max(lmin, 0); l < A.L; ++l) {
-    const int K = A.K[l];
-    if (K == 0) continue;
-    const int s = m >> (l + 1), nclus = 1 << (l + 1);
-    T* Cf = trans ? A.U[l] : A.V[l];
-    T* Ex = trans ? A.V[l] : A.U[l];
-    cbs[l] = DBuf<T>(c, (size_t)P * nclus * K * w);
-    c.tag = "mv_coef";
-    gemm<T>(c, K, w, s, P, nclus, T(1), opm<T>(Cf, 1, K, A.pps[l], (long)s * K),
-            opm<T>(W.p, W.ld, 1, W.ps, (long)s * W.ld), T(0), opm<T>(cbs[l].p, w, 1, (long)nclus * K * w, (long)K * w));
+  for (int l = 0; l < A.L; ++l) {
+    const int K = A.K[l], nc = ncol[l];
+    if (K == 0 || nc == 0) continue;
     const int i = ha.nl++;
-    ha.U[i] = Ex; ha.ups[i] = A.pps[l]; ha.C[i] = cbs[l].p; ha.K[i] = K; ha.s[i] = s; ha.nclus[i] = nclus;
+    ha.U[i] = trans ? A.V[l] : A.U[l];
+    ha.ups[i] = A.pps[l]; ha.C[i] = cbs[l].p; ha.K[i] = K; ha.s[i] = m >> (l + 1); ha.nclus[i] = 1 << (l + 1);
+    ha.ncol[i] = nc;
   }
   c.tag = "mv_expand";
   hexpand<T>(c, ha, P);
+}
+
+// Y = alpha * M^_{>=lmin} W + beta * Y  (trans: M^T): the leaf part and levels lmin.. of M.
+template <class T>
+void hmatvec(Ctx& c, const HMat<T>& A, int lmin, bool trans, Pan<T> W, Pan<T> Y, int w, T alpha, T beta) {
+  int ncol[MAXL] = {};
+  for (int l = std::max(lmin, 0); l < A.L; ++l) ncol[l] = w;
+  hmatvec_cols<T>(c, A, trans, W, Y, w, ncol, alpha, beta);
 }
 
 // Sum (Woodbury) form of the inverse of P HODLR matrices.
@@ -270,18 +281,31 @@ void flat_add_product(Ctx& c, Flat<T>& F, const HMat<T>& A, const HMat<T>& B, T 
   T* Y1[MAXL] = {};
   T* Y2[MAXL] = {};
   T* Wl[MAXL] = {};
+  long ld1 = 0, ld2 = 0;
+  // Y1[l] = A^{(>l)} U^B_l and Y2[l] = (B^{(>l)})^T V^A_l for every level at
+  // once: the panels of all levels side by side form one wide W, and level l'
+  // of the other factor touches only the columns of levels l < l' (a prefix).
+  for (int side = 0; side < 2; ++side) {
+    const HMat<T>& M = side ? B : A;     // the HODLR factor applied
+    const HMat<T>& Q = side ? A : B;     // whose panels are stacked
+    int off[MAXL + 1] = {};
+    for (int l = 0; l < L; ++l) off[l + 1] = off[l] + Q.K[l];
+    const int wt = off[L];
+    if (wt == 0) continue;
+    DBuf<T> Wc(c, (size_t)Pb * m * wt);
+    for (int l = 0; l < L; ++l)
+      if (Q.K[l] > 0)
+        copy2d<T>(c, Pb, m, Q.K[l], T(1), side ? Q.V[l] : Q.U[l], Q.K[l], Q.pps[l], Wc.p + off[l], wt, (long)m * wt);
+    F.owned.emplace_back(c, (size_t)Pb * m * wt);
+    T* Yall = F.owned.back().p;
+    hmatvec_cols<T>(c, M, side == 1, Pan<T>{Wc.p, wt, (long)m * wt}, Pan<T>{Yall, wt, (long)m * wt}, wt, off, T(1),
+                    T(0));
+    for (int l = 0; l < L; ++l)
+      if (Q.K[l] > 0) (side ? Y2 : Y1)[l] = Yall + off[l];
+    (side ? ld2 : ld1) = wt;
+  }
   for (int l = 0; l < L; ++l) {
     const int KA = A.K[l], KB = B.K[l], s = m >> (l + 1), nclus = 1 << (l + 1);
-    if (KB > 0) {
-      F.owned.emplace_back(c, (size_t)Pb * m * KB);
-      Y1[l] = F.owned.back().p;
-      hmatvec<T>(c, A, l + 1, false, Pan<T>{B.U[l], KB, B.pps[l]}, Pan<T>{Y1[l], KB, (long)m * KB}, KB, T(1), T(0));
-    }
-    if (KA > 0) {
-      F.owned.emplace_back(c, (size_t)Pb * m * KA);
-      Y2[l] = F.owned.back().p;
-      hmatvec<T>(c, B, l + 1, true, Pan<T>{A.V[l], KA, A.pps[l]}, Pan<T>{Y2[l], KA, (long)m * KA}, KA, T(1), T(0));
-    }
     if (KA > 0 && KB > 0) {
       DBuf<T> Tb(c, (size_t)Pb * nclus * KA * KB);
       c.tag = "prod_T";
@@ -308,8 +332,8 @@ void flat_add_product(Ctx& c, Flat<T>& F, const HMat<T>& A, const HMat<T>& B, T 
   }
   for (int l0 = 0; l0 < L; ++l0) {
     const int KA = A.K[l0], KB = B.K[l0];
-    if (KB > 0) F.lv[l0].push_back({Y1[l0], KB, (long)m * KB, B.V[l0], KB, B.pps[l0], KB, coef, Pb});
-    if (KA > 0) F.lv[l0].push_back({A.U[l0], KA, A.pps[l0], Y2[l0], KA, (long)m * KA, KA, coef, Pb});
+    if (KB > 0) F.lv[l0].push_back({Y1[l0], ld1, (long)m * ld1, B.V[l0], KB, B.pps[l0], KB, coef, Pb});
+    if (KA > 0) F.lv[l0].push_back({A.U[l0], KA, A.pps[l0], Y2[l0], ld2, (long)m * ld2, KA, coef, Pb});
     for (int l = 0; l < l0; ++l)
       if (Wl[l]) F.lv[l0].push_back({Wl[l], B.K[l], (long)m * B.K[l], B.V[l], B.K[l], B.pps[l], B.K[l], coef, Pb});
   }

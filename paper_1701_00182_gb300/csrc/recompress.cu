@@ -646,55 +646,66 @@ __global__ void __launch_bounds__(kQrcpThreads) k_qrcp(int r, const T* Call, con
 // Z (r x Kout, row major) per side of block bi such that the new factor is
 // factor * Z:  QR path  Z[0:k, t] = X[:, t] sqrt(s_t);  Gram path  Z[piv[u], t] = z[u],
 // R11 z = X[:, t] sqrt(s_t)  with R11[u][v] = R[u][piv[v]] (upper triangular).
+// Every row of Z is finally multiplied by the balancing scale of its column of
+// the original factor.
+//
+// One CTA per (side, block, chunk of C columns); its 256 threads are C columns
+// x G = 256 / C row groups.  The right-hand sides of the chunk sit in B (shared
+// memory when k x C fits, else a global scratch slice with row stride ldb).
+// Right-looking back substitution: at step u every thread forms
+// z_u = b_u / R11[u][u] for its column and removes z_u R11[w][u] from the rows
+// w < u of its group, so a step is one barrier and a k / G long update.
 template <class T>
-__global__ void __launch_bounds__(256) k_coef(int r, int Kout, long NB, int qr, const T* Rall, const int* pivall,
-                                              const int* kkall, const T* Xall, const T* Yall, const T* sigall,
-                                              const int* rankall, const T* scall, T* Zall, int smem_tri) {
+__global__ void __launch_bounds__(256) k_coef(int r, int Kout, long NB, int qr, const T* __restrict__ Rall,
+                                              const int* __restrict__ pivall, const int* __restrict__ kkall,
+                                              const T* __restrict__ Xall, const T* __restrict__ Yall,
+                                              const T* __restrict__ sigall, const int* __restrict__ rankall,
+                                              const T* __restrict__ scall, T* __restrict__ Zall, int C,
+                                              T* __restrict__ gscratch) {
   extern __shared__ unsigned char smraw[];
-  T* tri = reinterpret_cast<T*>(smraw);  // packed upper triangle of R11 (row u: entries v >= u)
   const long j = blockIdx.x;
   const int side = (int)(j / NB);
   const long bi = j % NB;
+  const int t0 = blockIdx.y * C;
+  const int tc = threadIdx.x % C, g = threadIdx.x / C, G = blockDim.x / C;
+  const int t = t0 + tc;
+  const int rank = rankall[bi];
+  const int k = kkall[j];
+  T* Z = Zall + j * (long)r * Kout;
+  if (t < Kout)
+    for (int row = g; row < r; row += G) Z[(long)row * Kout + t] = T(0);
+  if (t0 >= rank) return;  // uniform over the CTA
+  const bool act = t < rank;
   const T* R = Rall + j * (long)r * r;
   const int* piv = pivall + j * r;
-  const int k = kkall[j];
   const T* XY = (side ? Yall : Xall) + bi * (long)r * r;
-  const T* sig = sigall + bi * r;
-  const int rank = rankall[bi];
-  T* Z = Zall + j * (long)r * Kout;
-  for (long e = threadIdx.x; e < (long)r * Kout; e += blockDim.x) Z[e] = T(0);
-  const bool staged = !qr && (long)k * (k + 1) / 2 <= smem_tri;
-  if (staged) {
-    // row u starts at u*k - u*(u-1)/2; entry (u, v) at start + (v - u)
-    for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) {
-      int u = (int)(e / k), v = (int)(e % k);
-      if (v >= u) tri[(long)u * k - (long)u * (u - 1) / 2 + (v - u)] = R[(long)u * r + piv[v]];
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < rank; t += blockDim.x) {
-    const T sq = sqrt(sig[t]);
-    if (qr) {
-      for (int u = 0; u < k; ++u) Z[(long)u * Kout + t] = XY[(long)u * r + t] * sq;
-    } else if (staged) {
-      for (int u = k - 1; u >= 0; --u) {
-        const T* row = tri + (long)u * k - (long)u * (u - 1) / 2;
-        T v = XY[(long)u * r + t] * sq;
-        for (int w = u + 1; w < k; ++w) v -= row[w - u] * Z[(long)piv[w] * Kout + t];
-        Z[(long)piv[u] * Kout + t] = v / row[0];
-      }
-    } else {
-      for (int u = k - 1; u >= 0; --u) {
-        T v = XY[(long)u * r + t] * sq;
-        for (int w = u + 1; w < k; ++w) v -= R[(long)u * r + piv[w]] * Z[(long)piv[w] * Kout + t];
-        Z[(long)piv[u] * Kout + t] = v / R[(long)u * r + piv[u]];
-      }
-    }
-  }
-  if (scall) {
+  const T* sc = scall ? scall + j * (long)r : nullptr;
+  const T sq = act ? sqrt(sigall[bi * r + t]) : T(0);
+  if (qr) {
     __syncthreads();
-    const T* sc = scall + j * (long)r;  // side L: aL of block bi; side R: aR (both stored side-major)
-    for (long e = threadIdx.x; e < (long)r * Kout; e += blockDim.x) Z[e] *= sc[e / Kout];
+    if (act)
+      for (int u = g; u < k; u += G) Z[(long)u * Kout + t] = XY[(long)u * r + t] * sq * (sc ? sc[u] : T(1));
+    return;
+  }
+  T* B;
+  long ldb;
+  if (gscratch) {
+    ldb = (long)gridDim.y * C;  // padded so every thread of the grid owns its own column
+    B = gscratch + j * (long)r * ldb + t0;
+  } else {
+    B = reinterpret_cast<T*>(smraw);
+    ldb = C;
+  }
+  for (int u = g; u < k; u += G) B[(long)u * ldb + tc] = act ? XY[(long)u * r + t] * sq : T(0);
+  __syncthreads();  // also orders the zero fill of Z before the writes below
+  for (int u = k - 1; u >= 0; --u) {
+    const int pu = piv[u];
+    const T zu = B[(long)u * ldb + tc] / R[(long)u * r + pu];
+    const T* Rc = R + pu;
+#pragma unroll 4
+    for (int w = g; w < u; w += G) B[(long)w * ldb + tc] -= Rc[(long)w * r] * zu;
+    if (g == 0 && act) Z[(long)pu * Kout + t] = zu * (sc ? sc[pu] : T(1));
+    __syncthreads();
   }
 }
 
@@ -809,15 +820,37 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     return;
   }
   DBuf<T> Z(c, 2 * NB * (size_t)r * Kout);
+  DBuf<T> Bscr;
   c.kbegin();
   {
-    const size_t cap = 200 * 1024;
-    const long need = qr ? 0 : (long)r * (r + 1) / 2;
-    const int smem_tri = (int)std::min<long>(need, (long)(cap / sizeof(T)));
-    const size_t sm = (size_t)smem_tri * sizeof(T);
-    if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_coef<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_coef<T><<<(unsigned)(2 * NB), 256, sm, c.st>>>(r, Kout, NB, qr ? 1 : 0, R.p, piv.p, kk.p, Xo.p, Yo.p, sig.p,
-                                                    rank.p, scale.p, Z.p, smem_tri);
+    // column chunk: the widest of 32 / 16 / 8 whose k x C right-hand sides fit
+    // in 100 KB of shared memory (two CTAs per SM); else a global scratch.
+    int kmax = r;
+    if (!qr) {
+      std::vector<int> hk(2 * NB);
+      ACR_CUDA(cudaMemcpyAsync(hk.data(), kk.p, 2 * NB * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+      ACR_CUDA(cudaStreamSynchronize(c.st));
+      kmax = 0;
+      for (int v : hk) kmax = std::max(kmax, v);
+    }
+    const size_t cap = 100 * 1024;
+    int Cw = 32;
+    while (Cw > 8 && (size_t)kmax * Cw * sizeof(T) > cap) Cw /= 2;
+    size_t sm = 0;
+    T* gs = nullptr;
+    if (!qr) {
+      if ((size_t)kmax * Cw * sizeof(T) > cap) {
+        Bscr = DBuf<T>(c, 2 * NB * (size_t)r * (size_t)((Kout + Cw - 1) / Cw * Cw));
+        gs = Bscr.p;
+      } else {
+        sm = (size_t)kmax * Cw * sizeof(T);
+        if (sm > 48 * 1024)
+          ACR_CUDA(cudaFuncSetAttribute(k_coef<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      }
+    }
+    dim3 grid((unsigned)(2 * NB), (unsigned)((Kout + Cw - 1) / Cw));
+    k_coef<T><<<grid, 256, sm, c.st>>>(r, Kout, NB, qr ? 1 : 0, R.p, piv.p, kk.p, Xo.p, Yo.p, sig.p, rank.p,
+                                       scale.p, Z.p, Cw, gs);
   }
   c.kend(KC_COEF, 0, 2.0 * NB * sizeof(T) * ((double)r * r + (double)r * Kout));
   Uout = DBuf<T>(c, (size_t)P * m * Kout);

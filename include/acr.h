@@ -29,7 +29,9 @@
  * Errors.  Every int-returning call returns ACR_OK (0) or one of the
  * ACR_ERR_* codes below; acr_error_string gives a message.  No call traps the
  * GPU; a numerical breakdown inside a kernel (a zero leaf pivot) is recorded
- * in a device flag and reported as ACR_ERR_BREAKDOWN.
+ * in a device flag and reported as ACR_ERR_BREAKDOWN.  Every wait inside a
+ * kernel (tensor-core MMA completion) is bounded in time; one that expires is
+ * recorded in a device flag and reported by acr_factor as ACR_ERR_CUDA.
  */
 #ifndef ACR_H_
 #define ACR_H_

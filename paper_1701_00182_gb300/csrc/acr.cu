@@ -216,6 +216,10 @@ void check_flag(acr_handle_s* h) {
   ACR_CUDA(cudaMemcpyAsync(fl, h->ctx.d_flag, sizeof(fl), cudaMemcpyDeviceToHost, h->ctx.st));
   ACR_CUDA(cudaStreamSynchronize(h->ctx.st));
   h->stats.jacobi_sweeps_max = fl[1];
+  if (fl[2]) {
+    ACR_CUDA(cudaMemsetAsync(h->ctx.d_flag + 2, 0, sizeof(int), h->ctx.st));
+    throw AcrError(ACR_ERR_CUDA, "a tensor-core GEMM gave up waiting for its MMAs (time limit)");
+  }
   const int f = fl[0];
   if (f) {
     ACR_CUDA(cudaMemsetAsync(h->ctx.d_flag, 0, sizeof(int), h->ctx.st));
@@ -672,6 +676,8 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     c.budget = o.mem_budget;
     const char* cb = std::getenv("ACR_CHECK_BOUNDS");
     c.check_bounds = cb && cb[0] == '1';
+    const char* fc = std::getenv("ACR_GEMM_CFG");
+    c.force_cfg = fc ? std::atoi(fc) : -1;
     c.autotune = o.autotune != 0;
     c.profile = o.profile != 0;
     c.inverse_fp64 = o.inverse_fp64 != 0;

@@ -54,10 +54,11 @@ struct Ctx {
   bool autotune = false;
   std::vector<std::pair<unsigned long long, int>> tuned;  // shape key -> config
   std::map<uintptr_t, size_t> live;  // allocation start -> bytes (for the operand extent check)
-  bool check_bounds = false;
-  bool inverse_fp64 = false;
-  bool tensor = false;
-  int core_svd = 0;                  // 0 auto (QRCP for FP32, Jacobi SVD for FP64), 1 Jacobi, 2 QRCP               // FP32 GEMMs of large tiles on the tensor pipe (3xTF32)         // FP32 factorisation: leaf and coupling inverses in FP64         // ACR_CHECK_BOUNDS=1: verify every GEMM operand range on the host
+  bool check_bounds = false;  // ACR_CHECK_BOUNDS=1: verify every GEMM operand range on the host
+  bool inverse_fp64 = false;  // FP32 factorisation: leaf and coupling inverses in FP64
+  bool tensor = false;        // FP32 GEMMs of large tiles on the tensor cores (3xTF32)
+  int force_cfg = -1;         // ACR_GEMM_CFG=<i>: every GEMM uses tiling i where it is valid (debugging)
+  int core_svd = 0;           // core truncation: 0 auto (pivoted QR in FP32, Jacobi SVD in FP64), 1 Jacobi, 2 pivoted QR
   void check_range(const void* base, long lo, long hi, size_t es, const char* what) const;
   bool profile = false;  // record CUDA events around every launch, accumulated per kernel class
   double kc_ms[16] = {}, kc_flops[16] = {}, kc_bytes[16] = {};

@@ -421,15 +421,263 @@ __global__ void k_scale_c(GArgs<T> g) {
   }
 }
 
+// ---- FP32 GEMM on the 5th-generation tensor cores (3xTF32) ---------------------
+// 128 x 128 output tile per CTA, accumulated in tensor memory (128 lanes x 128
+// FP32 columns).  Each 32-deep K slice of A and B is loaded by the 256 threads
+// (any strides, zero fill outside the operand), split into a TF32 high part
+// and the rounded remainder, and stored K-major in the 128-byte-swizzled
+// layout the tensor core reads (row r, 16-byte chunk q at r*128 + (q^(r%8))*16,
+// 8-row atoms 1 KB apart).  One thread then issues A_hi B_hi + A_hi B_lo +
+// A_lo B_hi as 3 x 4 MMAs of 128 x 128 x 8 and commits them to the slice's
+// mbarrier; two slices are in flight, so the global loads of slice k+1
+// overlap the MMAs of slice k.  The epilogue reads the accumulator with
+// tcgen05.ld (warp w: lanes 32 (w mod 4) .. +31, columns 64 (w / 4) .. +63).
+// Every mbarrier wait is bounded in time; on expiry the kernel sets an error
+// flag, skips its epilogue and still frees its tensor memory.
+namespace tc {
+constexpr int BM = 128, BN = 128, BK = 32;
+constexpr int TILE_BYTES = BM * BK * 4;      // 128 rows x 128 B
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A_hi, A_lo, B_hi, B_lo
+constexpr int NSTAGE = 2;
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;  // + slack for the 1 KB alignment
+constexpr uint32_t TMEM_COLS = 128;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+// instruction descriptor: D F32, A and B TF32, both K-major, N >> 3, M >> 4
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}  // namespace tc
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Shared-memory matrix descriptor: start address, leading byte offset 16 (not
+// used by a swizzled K-major operand), stride byte offset 1024 (next 8-row
+// atom), descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  unsigned long long t0 = 0;
+  for (int it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it == 0) t0 = global_ns();
+    else if ((it & 31) == 0 && global_ns() - t0 > tc::WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(256, 1) k_gemm_tc05(GArgs<float> g, int* err) {
+  extern __shared__ unsigned char tc_raw[];
+  __shared__ __align__(8) uint64_t bars[tc::NSTAGE];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int bi = blockIdx.x;
+  const int plane = bi / g.nclus, c = bi - plane * g.nclus;
+  const int tilesN = (g.N + tc::BN - 1) / tc::BN;
+  const int m0 = (blockIdx.y / tilesN) * tc::BM, n0 = (blockIdx.y % tilesN) * tc::BN;
+  if (g.sym && m0 >= n0 + tc::BN) return;  // tile strictly below the diagonal (uniform)
+  const int kbeg = blockIdx.z * g.kchunk;
+  const int kend = min(g.K, kbeg + g.kchunk);
+  const int nk = kend > kbeg ? (kend - kbeg + tc::BK - 1) / tc::BK : 0;
+  const uint32_t raw_s = smem_u32(tc_raw);
+  const uint32_t base_s = (raw_s + 1023u) & ~1023u;
+  unsigned char* base = tc_raw + (base_s - raw_s);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(tc::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < tc::NSTAGE; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_ok = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  const float* A = opaddr(g.A, plane, c);
+  const float* B = opaddr(g.B, plane, c);
+  const long ars = g.A.rs, acs = g.A.cs, brs = g.B.rs, bcs = g.B.cs;
+  const bool a_kfast = (acs == 1), b_kfast = (brs == 1);
+  // Each thread owns 4 quads (4 consecutive k of one row) of A and of B per
+  // slice.  Lanes run along the contiguous global direction of the operand.
+  float ra[4][4], rb[4][4];
+  auto quad = [&](bool kfast, int it, int& row, int& q) {
+    const int e = tid + 256 * it;
+    if (kfast) { row = e >> 3; q = e & 7; } else { row = e & 127; q = e >> 7; }
+  };
+  auto load = [&](int kc) {
+    const int k0 = kbeg + kc * tc::BK;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      int row, q;
+      quad(a_kfast, it, row, q);
+      const int gi = m0 + row;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gk = k0 + 4 * q + j;
+        ra[it][j] = (gi < g.M && gk < kend) ? A[(long)gi * ars + (long)gk * acs] : 0.f;
+      }
+      quad(b_kfast, it, row, q);
+      const int gj = n0 + row;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gk = k0 + 4 * q + j;
+        rb[it][j] = (gj < g.N && gk < kend) ? B[(long)gk * brs + (long)gj * bcs] : 0.f;
+      }
+    }
+  };
+  auto store = [&](int s) {
+    unsigned char* st = base + s * tc::STAGE_BYTES;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      int row, q;
+      quad(a_kfast, it, row, q);
+      uint32_t off = row * 128 + ((q ^ (row & 7)) << 4);
+      float4 h, l;
+      h.x = tf32_rna(ra[it][0]); l.x = tf32_rna(ra[it][0] - h.x);
+      h.y = tf32_rna(ra[it][1]); l.y = tf32_rna(ra[it][1] - h.y);
+      h.z = tf32_rna(ra[it][2]); l.z = tf32_rna(ra[it][2] - h.z);
+      h.w = tf32_rna(ra[it][3]); l.w = tf32_rna(ra[it][3] - h.w);
+      *reinterpret_cast<float4*>(st + off) = h;
+      *reinterpret_cast<float4*>(st + tc::TILE_BYTES + off) = l;
+      quad(b_kfast, it, row, q);
+      off = row * 128 + ((q ^ (row & 7)) << 4);
+      h.x = tf32_rna(rb[it][0]); l.x = tf32_rna(rb[it][0] - h.x);
+      h.y = tf32_rna(rb[it][1]); l.y = tf32_rna(rb[it][1] - h.y);
+      h.z = tf32_rna(rb[it][2]); l.z = tf32_rna(rb[it][2] - h.z);
+      h.w = tf32_rna(rb[it][3]); l.w = tf32_rna(rb[it][3] - h.w);
+      *reinterpret_cast<float4*>(st + 2 * tc::TILE_BYTES + off) = h;
+      *reinterpret_cast<float4*>(st + 3 * tc::TILE_BYTES + off) = l;
+    }
+  };
+
+  if (nk > 0) load(0);
+  for (int kc = 0; kc < nk; ++kc) {
+    const int s = kc & 1;
+    if (kc >= 2 && tid == 0 && !mbar_wait_bounded(smem_u32(&bars[s]), ((kc - 2) >> 1) & 1)) s_ok = 0;
+    __syncthreads();  // stage s is free again (its MMAs of slice kc-2 completed)
+    if (!s_ok) break;
+    store(s);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();  // stage s written and visible to the tensor core
+    if (kc + 1 < nk) load(kc + 1);
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = base_s + s * tc::STAGE_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < tc::BK / 8; ++kk) {
+        const uint64_t ah = umma_desc_sw128(sa + kk * 32), al = umma_desc_sw128(sa + tc::TILE_BYTES + kk * 32);
+        const uint64_t bh = umma_desc_sw128(sa + 2 * tc::TILE_BYTES + kk * 32),
+                       bl = umma_desc_sw128(sa + 3 * tc::TILE_BYTES + kk * 32);
+        umma_tf32(tmem, ah, bh, tc::IDESC, (kc > 0 || kk > 0) ? 1u : 0u);
+        umma_tf32(tmem, ah, bl, tc::IDESC, 1u);
+        umma_tf32(tmem, al, bh, tc::IDESC, 1u);
+      }
+      umma_commit(smem_u32(&bars[s]));
+    }
+  }
+  if (nk > 0 && tid == 0 && s_ok && !mbar_wait_bounded(smem_u32(&bars[(nk - 1) & 1]), ((nk - 1) >> 1) & 1)) s_ok = 0;
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (s_ok) {
+    const int lb = (warp & 3) * 32, cb = (warp >> 2) * 64;
+    const int gi = m0 + lb + lane;
+#pragma unroll 1
+    for (int ch = 0; ch < 4; ++ch) {
+      uint32_t r[16];
+      if (nk > 0) {
+        tmem_ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)(cb + ch * 16), r);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) r[j] = 0u;
+      }
+      if (gi < g.M) {
+        if (g.partial) {
+          float* P = g.partial + ((long)blockIdx.z * g.batch + bi) * (long)g.M * g.N + (long)gi * g.N;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int gj = n0 + cb + ch * 16 + j;
+            if (gj < g.N) P[gj] = __uint_as_float(r[j]);
+          }
+        } else {
+          float* C = opaddr(g.C, plane, c) + (long)gi * g.C.rs;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int gj = n0 + cb + ch * 16 + j;
+            if (gj >= g.N) continue;
+            float* cp = C + (long)gj * g.C.cs;
+            float v = g.alpha * __uint_as_float(r[j]);
+            if (g.beta != 0.f) v += g.beta * *cp;
+            *cp = v;
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::TMEM_COLS));
+}
+
 namespace {
 
 struct Cfg {
   int bm, bn, bk;
 };
-constexpr Cfg kCfg[6] = {{64, 64, 16}, {128, 64, 8}, {32, 32, 32}, {128, 128, 8}, {128, 128, 8}, {128, 128, 16}};
+constexpr int kNCfg = 7;
+constexpr Cfg kCfg[kNCfg] = {{64, 64, 16},   {128, 64, 8},   {32, 32, 32},  {128, 128, 8},
+                             {128, 128, 8}, {128, 128, 16}, {128, 128, 32}};
+
+// Configurations 5 (mma.sync 3xTF32) and 6 (tcgen05 3xTF32) exist for FP32 only.
+bool cfg_valid(int cfg, int es, bool tensor) { return cfg < 5 || (tensor && es == 4); }
 
 template <class T>
-void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st) {
+void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st, int* err) {
   switch (cfg) {
     case 0: k_gemm<T, 64, 64, 16, 4, 4><<<grid, 256, 0, st>>>(g); break;
     case 1: k_gemm<T, 128, 64, 8, 8, 4><<<grid, 256, 0, st>>>(g); break;
@@ -439,16 +687,24 @@ void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st) {
       if constexpr (sizeof(T) == 4) k_gemm_f32_big<<<grid, 256, 0, st>>>(g);
       else k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g);
       break;
-    default:
+    case 5:
       if constexpr (sizeof(T) == 4) k_gemm_tf32x3<<<grid, 256, 0, st>>>(g);
       else k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g);
+      break;
+    default:
+      if constexpr (sizeof(T) == 4) {
+        ACR_CUDA(cudaFuncSetAttribute(k_gemm_tc05, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+        k_gemm_tc05<<<grid, 256, tc::SMEM_BYTES, st>>>(g, err);
+      } else {
+        k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g);
+      }
       break;
   }
 }
 
 int heuristic_cfg(int M, int N, long batch, int es, bool tensor) {
   if (M <= 32 && N <= 32) return 2;
-  if (M >= 96 && N >= 96) return es == 4 ? (tensor ? 5 : 4) : 3;
+  if (M >= 96 && N >= 96) return es == 4 ? (tensor ? 6 : 4) : 3;
   if (M >= 128 && N <= 64) return 1;
   return 0;
 }
@@ -485,7 +741,7 @@ static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch
     g.partial = part;
     const double es = sizeof(T);
     c.kbegin();
-    launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, split), g, c.st);
+    launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, split), g, c.st, c.d_flag + 2);
     c.kend(KC_GEMM, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch, es * batch * ((double)M * K + (double)K * N + (double)M * N * split));
     long tot = batch * (long)M * N;
     int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
@@ -497,7 +753,7 @@ static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch
     g.kchunk = K;
     g.partial = nullptr;
     c.kbegin();
-    launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, 1), g, c.st);
+    launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, 1), g, c.st, c.d_flag + 2);
     c.kend(KC_GEMM, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch,
            (double)sizeof(T) * batch * ((double)M * K + (double)K * N + (double)M * N * (1 + (g.beta != T(0)))));
   }
@@ -551,7 +807,10 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
   GArgs<T> g{M, N, K, nclus, (int)batch, alpha, beta, A, B, C, K, nullptr, sym};
   int cfg = heuristic_cfg(M, N, batch, (int)sizeof(T), c.tensor);
   int split = split_for(cfg, M, N, K, batch);
-  if (c.autotune) {
+  if (c.force_cfg >= 0 && c.force_cfg < kNCfg && cfg_valid(c.force_cfg, (int)sizeof(T), c.tensor)) {
+    cfg = c.force_cfg;
+    split = split_for(cfg, M, N, K, batch);
+  } else if (c.autotune) {
     unsigned long long key = shape_key(sizeof(T), M, N, K, batch);
     int found = -1;
     {
@@ -572,11 +831,11 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
       ACR_CUDA(cudaEventCreate(&e1));
       float best = 1e30f;
       int bestc = 0;
-      for (int cand = 0; cand < 12; ++cand) {
-        int cf = cand % 6;
-        if (cf == 5 && !(c.tensor && sizeof(T) == 4)) continue;
-        int sp = (cand / 6) ? split_for(cf, M, N, K, batch) : 1;
-        if ((cand / 6) && sp == 1) continue;
+      for (int cand = 0; cand < 2 * kNCfg; ++cand) {
+        int cf = cand % kNCfg;
+        if (!cfg_valid(cf, (int)sizeof(T), c.tensor)) continue;
+        int sp = (cand / kNCfg) ? split_for(cf, M, N, K, batch) : 1;
+        if ((cand / kNCfg) && sp == 1) continue;
         run_gemm<T>(c, cf, sp, M, N, K, batch, gt);  // warm
         ACR_CUDA(cudaEventRecord(e0, c.st));
         run_gemm<T>(c, cf, sp, M, N, K, batch, gt);
@@ -593,8 +852,8 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tuned.push_back({key, found});
     }
-    cfg = found % 6;
-    split = (found / 6) ? split_for(cfg, M, N, K, batch) : 1;
+    cfg = found % kNCfg;
+    split = (found / kNCfg) ? split_for(cfg, M, N, K, batch) : 1;
   }
   run_gemm<T>(c, cfg, split, M, N, K, batch, g);
   if (sym) {

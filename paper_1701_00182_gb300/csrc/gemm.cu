@@ -429,8 +429,8 @@ __global__ void k_scale_c(GArgs<T> g) {
 // layout the tensor core reads (row r, 16-byte chunk q at r*128 + (q^(r%8))*16,
 // 8-row atoms 1 KB apart).  One thread then issues A_hi B_hi + A_hi B_lo +
 // A_lo B_hi as 3 x 4 MMAs of 128 x 128 x 8 and commits them to the slice's
-// mbarrier; two slices are in flight, so the global loads of slice k+1
-// overlap the MMAs of slice k.  The epilogue reads the accumulator with
+// mbarrier.  Three shared-memory stages and two register sets keep the global
+// loads of slices k+1 and k+2 in flight while the MMAs of slice k run.  The epilogue reads the accumulator with
 // tcgen05.ld (warp w: lanes 32 (w mod 4) .. +31, columns 64 (w / 4) .. +63).
 // Every mbarrier wait is bounded in time; on expiry the kernel sets an error
 // flag, skips its epilogue and still frees its tensor memory.
@@ -438,7 +438,7 @@ namespace tc {
 constexpr int BM = 128, BN = 128, BK = 32;
 constexpr int TILE_BYTES = BM * BK * 4;      // 128 rows x 128 B
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A_hi, A_lo, B_hi, B_lo
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 3;
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;  // + slack for the 1 KB alignment
 constexpr uint32_t TMEM_COLS = 128;
 constexpr unsigned long long WAIT_NS = 2000000000ull;
@@ -489,12 +489,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
   }
 }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -543,83 +537,102 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc05(GArgs<float> g, int* err) 
   const bool a_kfast = (acs == 1), b_kfast = (brs == 1);
   // Each thread owns 4 quads (4 consecutive k of one row) of A and of B per
   // slice.  Lanes run along the contiguous global direction of the operand.
-  float ra[4][4], rb[4][4];
-  auto quad = [&](bool kfast, int it, int& row, int& q) {
+  // Two register sets hold the slices k+1 and k+2 while slice k is stored.
+  float ra0[4][4], rb0[4][4], ra1[4][4], rb1[4][4];
+  // Fixed per thread for the whole K loop: the rows it loads, their first
+  // element, whether they exist, and where their quads go in a stage.
+  const float* pa[4];
+  const float* pb[4];
+  bool va[4], vb[4];
+  int qa[4], qb[4];
+  uint32_t oa[4], ob[4];
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
     const int e = tid + 256 * it;
-    if (kfast) { row = e >> 3; q = e & 7; } else { row = e & 127; q = e >> 7; }
-  };
-  auto load = [&](int kc) {
-    const int k0 = kbeg + kc * tc::BK;
+    int row = a_kfast ? (e >> 3) : (e & 127), q = a_kfast ? (e & 7) : (e >> 7);
+    va[it] = m0 + row < g.M;
+    qa[it] = 4 * q;
+    pa[it] = A + (long)(va[it] ? m0 + row : 0) * ars + (long)(kbeg + 4 * q) * acs;
+    oa[it] = row * 128 + ((q ^ (row & 7)) << 4);
+    row = b_kfast ? (e >> 3) : (e & 127);
+    q = b_kfast ? (e & 7) : (e >> 7);
+    vb[it] = n0 + row < g.N;
+    qb[it] = 4 * q;
+    pb[it] = B + (long)(vb[it] ? n0 + row : 0) * bcs + (long)(kbeg + 4 * q) * brs;
+    ob[it] = row * 128 + ((q ^ (row & 7)) << 4);
+  }
+  auto load = [&](int kc, float (&ra)[4][4], float (&rb)[4][4]) {
+    const int kr = kend - kbeg - kc * tc::BK;  // k rows left in this slice (relative)
+    const long ka = (long)kc * tc::BK * acs, kb = (long)kc * tc::BK * brs;
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
-      int row, q;
-      quad(a_kfast, it, row, q);
-      const int gi = m0 + row;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int gk = k0 + 4 * q + j;
-        ra[it][j] = (gi < g.M && gk < kend) ? A[(long)gi * ars + (long)gk * acs] : 0.f;
-      }
-      quad(b_kfast, it, row, q);
-      const int gj = n0 + row;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int gk = k0 + 4 * q + j;
-        rb[it][j] = (gj < g.N && gk < kend) ? B[(long)gk * brs + (long)gj * bcs] : 0.f;
+        ra[it][j] = (va[it] && qa[it] + j < kr) ? pa[it][ka + j * acs] : 0.f;
+        rb[it][j] = (vb[it] && qb[it] + j < kr) ? pb[it][kb + j * brs] : 0.f;
       }
     }
   };
-  auto store = [&](int s) {
+  // TF32 high part rounded to nearest (ties away from zero: add half an ulp of
+  // bit 13 to the magnitude, clear the low 13 bits), and the rounded remainder.
+  auto split4 = [](const float (&x)[4], float4& h, float4& l) {
+    auto hi = [](float v) { return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u); };
+    h.x = hi(x[0]); l.x = hi(x[0] - h.x);
+    h.y = hi(x[1]); l.y = hi(x[1] - h.y);
+    h.z = hi(x[2]); l.z = hi(x[2] - h.z);
+    h.w = hi(x[3]); l.w = hi(x[3] - h.w);
+  };
+  auto store = [&](int s, const float (&ra)[4][4], const float (&rb)[4][4]) {
     unsigned char* st = base + s * tc::STAGE_BYTES;
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
-      int row, q;
-      quad(a_kfast, it, row, q);
-      uint32_t off = row * 128 + ((q ^ (row & 7)) << 4);
       float4 h, l;
-      h.x = tf32_rna(ra[it][0]); l.x = tf32_rna(ra[it][0] - h.x);
-      h.y = tf32_rna(ra[it][1]); l.y = tf32_rna(ra[it][1] - h.y);
-      h.z = tf32_rna(ra[it][2]); l.z = tf32_rna(ra[it][2] - h.z);
-      h.w = tf32_rna(ra[it][3]); l.w = tf32_rna(ra[it][3] - h.w);
-      *reinterpret_cast<float4*>(st + off) = h;
-      *reinterpret_cast<float4*>(st + tc::TILE_BYTES + off) = l;
-      quad(b_kfast, it, row, q);
-      off = row * 128 + ((q ^ (row & 7)) << 4);
-      h.x = tf32_rna(rb[it][0]); l.x = tf32_rna(rb[it][0] - h.x);
-      h.y = tf32_rna(rb[it][1]); l.y = tf32_rna(rb[it][1] - h.y);
-      h.z = tf32_rna(rb[it][2]); l.z = tf32_rna(rb[it][2] - h.z);
-      h.w = tf32_rna(rb[it][3]); l.w = tf32_rna(rb[it][3] - h.w);
-      *reinterpret_cast<float4*>(st + 2 * tc::TILE_BYTES + off) = h;
-      *reinterpret_cast<float4*>(st + 3 * tc::TILE_BYTES + off) = l;
+      split4(ra[it], h, l);
+      *reinterpret_cast<float4*>(st + oa[it]) = h;
+      *reinterpret_cast<float4*>(st + tc::TILE_BYTES + oa[it]) = l;
+      split4(rb[it], h, l);
+      *reinterpret_cast<float4*>(st + 2 * tc::TILE_BYTES + ob[it]) = h;
+      *reinterpret_cast<float4*>(st + 3 * tc::TILE_BYTES + ob[it]) = l;
     }
   };
-
-  if (nk > 0) load(0);
-  for (int kc = 0; kc < nk; ++kc) {
-    const int s = kc & 1;
-    if (kc >= 2 && tid == 0 && !mbar_wait_bounded(smem_u32(&bars[s]), ((kc - 2) >> 1) & 1)) s_ok = 0;
-    __syncthreads();  // stage s is free again (its MMAs of slice kc-2 completed)
-    if (!s_ok) break;
-    store(s);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();  // stage s written and visible to the tensor core
-    if (kc + 1 < nk) load(kc + 1);
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = base_s + s * tc::STAGE_BYTES;
+  auto issue = [&](int kc, int s) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t sa = base_s + s * tc::STAGE_BYTES;
 #pragma unroll
-      for (int kk = 0; kk < tc::BK / 8; ++kk) {
-        const uint64_t ah = umma_desc_sw128(sa + kk * 32), al = umma_desc_sw128(sa + tc::TILE_BYTES + kk * 32);
-        const uint64_t bh = umma_desc_sw128(sa + 2 * tc::TILE_BYTES + kk * 32),
-                       bl = umma_desc_sw128(sa + 3 * tc::TILE_BYTES + kk * 32);
-        umma_tf32(tmem, ah, bh, tc::IDESC, (kc > 0 || kk > 0) ? 1u : 0u);
-        umma_tf32(tmem, ah, bl, tc::IDESC, 1u);
-        umma_tf32(tmem, al, bh, tc::IDESC, 1u);
-      }
-      umma_commit(smem_u32(&bars[s]));
+    for (int kk = 0; kk < tc::BK / 8; ++kk) {
+      const uint64_t ah = umma_desc_sw128(sa + kk * 32), al = umma_desc_sw128(sa + tc::TILE_BYTES + kk * 32);
+      const uint64_t bh = umma_desc_sw128(sa + 2 * tc::TILE_BYTES + kk * 32),
+                     bl = umma_desc_sw128(sa + 3 * tc::TILE_BYTES + kk * 32);
+      umma_tf32(tmem, ah, bh, tc::IDESC, (kc > 0 || kk > 0) ? 1u : 0u);
+      umma_tf32(tmem, ah, bl, tc::IDESC, 1u);
+      umma_tf32(tmem, al, bh, tc::IDESC, 1u);
     }
+    umma_commit(smem_u32(&bars[s]));
+  };
+  // One step: wait until the MMAs that last read stage kc % NSTAGE are done,
+  // store slice kc there, one barrier (which also votes on the waits), start
+  // the loads of slice kc + 2 into the freed registers, issue the MMAs.
+  auto step = [&](int kc, float (&ra)[4][4], float (&rb)[4][4]) -> bool {
+    const int s = kc % tc::NSTAGE;
+    bool ok = true;
+    if (kc >= tc::NSTAGE) ok = mbar_wait_bounded(smem_u32(&bars[s]), ((kc - tc::NSTAGE) / tc::NSTAGE) & 1);
+    if (ok) store(s, ra, rb);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (!__syncthreads_and(ok)) return false;
+    if (kc + 2 < nk) load(kc + 2, ra, rb);
+    if (tid == 0) issue(kc, s);
+    return true;
+  };
+
+  bool ok = true;
+  if (nk > 0) load(0, ra0, rb0);
+  if (nk > 1) load(1, ra1, rb1);
+  for (int kc = 0; kc < nk && ok; kc += 2) {
+    ok = step(kc, ra0, rb0);
+    if (ok && kc + 1 < nk) ok = step(kc + 1, ra1, rb1);
   }
-  if (nk > 0 && tid == 0 && s_ok && !mbar_wait_bounded(smem_u32(&bars[(nk - 1) & 1]), ((nk - 1) >> 1) & 1)) s_ok = 0;
+  if (ok && nk > 0) ok = mbar_wait_bounded(smem_u32(&bars[(nk - 1) % tc::NSTAGE]), ((nk - 1) / tc::NSTAGE) & 1);
+  if (!__syncthreads_and(ok)) s_ok = 0;
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (s_ok) {

@@ -192,7 +192,15 @@ def roofline(kernels, precision, peaks, source):
     ai = kc["flops"] / kc["bytes"] if kc["bytes"] else 0.0
     ridge = alu_peak * 1e12 / (hbm * 1e9)
     per_launch = kc["bytes"] / max(kc["launches"], 1)
-    if kc["flops"] > 0 and ai >= ridge:
+    if name == "gemm_tcgen05":
+        # FP32 products as three TF32 MMAs each: the tensor-pipe ceiling in FP32
+        # flops is the TF32 dense rate / 3; TF32 = measured sustained BF16 x the
+        # nominal TF32 : BF16 ratio (1.1 : 2.25 PFLOP/s dense).
+        tf32 = peaks["bf16_tflops_sustained"] * (1.1 / 2.25)
+        peak = tf32 / 3.0
+        out = {"bound": "tensor", "achieved": tfs, "peak": peak, "unit": "TFLOP/s", "frac": tfs / peak,
+               "peak_source": "%s bf16_tflops_sustained x 1.1/2.25 (TF32) / 3 (3xTF32 passes)" % source}
+    elif kc["flops"] > 0 and ai >= ridge:
         out = {"bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfs / alu_peak,
                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz
                if precision == "f32" else "nominal FP64 rate of the recipe"}

@@ -68,8 +68,9 @@ void Ctx::kend(int cls, double flops, double bytes) {
   cudaEvent_t b = evfree.back();
   evfree.pop_back();
   ACR_CUDA(cudaEventRecord(b, st));
-  pend.push_back({evcur, b, cls, cls == KC_GEMM ? tag : nullptr});
-  if (cls == KC_GEMM) site[tag].second += flops;
+  const bool g = cls == KC_GEMM || cls == KC_GEMM_TC || cls == KC_HEXPAND;
+  pend.push_back({evcur, b, cls, g ? tag : nullptr});
+  if (g) site[tag].second += flops;
   evcur = nullptr;
   if (pend.size() >= 8192) kflush();
 }
@@ -169,7 +170,7 @@ struct acr_handle_s {
     coef.release();
     if (ctx.st) cudaStreamSynchronize(ctx.st);
     const char* ps = std::getenv("ACR_PROFILE_SITES");
-    if (ps && ps[0] == '1' && !ctx.site.empty()) {
+    if (ps && (ps[0] == '1' || ps[0] == '2') && !ctx.site.empty()) {
       ctx.kflush();
       for (auto& kv : ctx.site)
         std::fprintf(stderr, "acr gemm site %-14s %10.1f ms %10.3f TFLOP\n", kv.first.c_str(), kv.second.first,
@@ -676,6 +677,8 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     c.budget = o.mem_budget;
     const char* cb = std::getenv("ACR_CHECK_BOUNDS");
     c.check_bounds = cb && cb[0] == '1';
+    const char* sd = std::getenv("ACR_PROFILE_SITES");
+    c.site_detail = sd && sd[0] == '2';
     const char* fc = std::getenv("ACR_GEMM_CFG");
     c.force_cfg = fc ? std::atoi(fc) : -1;
     c.autotune = o.autotune != 0;

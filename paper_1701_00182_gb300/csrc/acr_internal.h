@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <map>
+#include <set>
 #include <string>
 #include <cstdio>
 #include <stdexcept>
@@ -41,7 +42,7 @@ struct AcrError : std::runtime_error {
 
 // Kernel classes for the per-class profile (CUDA events on the launch stream).
 enum KClass { KC_GEMM, KC_SPLITK, KC_QR, KC_PCHOL, KC_JACOBI, KC_COEF, KC_GJ, KC_COPY, KC_ASSEMBLE, KC_PERMUTE,
-              KC_STENCIL, KC_N };
+              KC_STENCIL, KC_GEMM_TC, KC_HEXPAND, KC_N };
 
 // Execution context of one handle: stream, scratch, counters, autotune cache.
 struct Ctx {
@@ -65,6 +66,8 @@ struct Ctx {
   long long kc_launch[16] = {};
   struct PendingEv { cudaEvent_t a, b; int cls; const char* tag; };
   const char* tag = "other";  // call site of the next GEMM (profile breakdown)
+  bool site_detail = false;   // ACR_PROFILE_SITES=2: split each site by GEMM shape and tiling
+  std::set<std::string> tagstore;
   std::map<std::string, std::pair<double, double>> site;  // tag -> (ms, flops)
   std::vector<cudaEvent_t> evfree;
   std::vector<PendingEv> pend;

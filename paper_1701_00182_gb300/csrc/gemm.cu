@@ -9,6 +9,7 @@
 // measured once with CUDA events and cached for the process.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <mutex>
 
 #include "acr_internal.h"
@@ -716,6 +717,7 @@ void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st, int* err
 }
 
 int heuristic_cfg(int M, int N, long batch, int es, bool tensor) {
+  if (es == 4 && tensor && M >= 64 && N >= 32) return 6;
   if (M <= 32 && N <= 32) return 2;
   if (M >= 96 && N >= 96) return es == 4 ? (tensor ? 6 : 4) : 3;
   if (M >= 128 && N <= 64) return 1;
@@ -743,6 +745,7 @@ unsigned long long shape_key(int es, int M, int N, int K, long batch) {
 template <class T>
 static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch, GArgs<T> g) {
   const Cfg& f = kCfg[cfg];
+  const KClass cls = (cfg == 6 && sizeof(T) == 4) ? KC_GEMM_TC : KC_GEMM;
   int tiles = ((M + f.bm - 1) / f.bm) * ((N + f.bn - 1) / f.bn);
   if (split > 1) {
     int kchunk = (K + split - 1) / split;
@@ -755,7 +758,7 @@ static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch
     const double es = sizeof(T);
     c.kbegin();
     launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, split), g, c.st, c.d_flag + 2);
-    c.kend(KC_GEMM, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch, es * batch * ((double)M * K + (double)K * N + (double)M * N * split));
+    c.kend(cls, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch, es * batch * ((double)M * K + (double)K * N + (double)M * N * split));
     long tot = batch * (long)M * N;
     int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
     c.kbegin();
@@ -767,7 +770,7 @@ static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch
     g.partial = nullptr;
     c.kbegin();
     launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, 1), g, c.st, c.d_flag + 2);
-    c.kend(KC_GEMM, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch,
+    c.kend(cls, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch,
            (double)sizeof(T) * batch * ((double)M * K + (double)K * N + (double)M * N * (1 + (g.beta != T(0)))));
   }
 }
@@ -867,6 +870,11 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
     }
     cfg = found % kNCfg;
     split = (found / kNCfg) ? split_for(cfg, M, N, K, batch) : 1;
+  }
+  if (c.profile && c.site_detail) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "%s M%d N%d K%d b%ld c%d s%d", c.tag, M, N, K, batch, cfg, split);
+    c.tag = c.tagstore.insert(buf).first->c_str();
   }
   run_gemm<T>(c, cfg, split, M, N, K, batch, g);
   if (sym) {
@@ -993,7 +1001,7 @@ void hexpand(Ctx& c, const HexpArgs<T>& a, int P) {
   for (int l = 0; l < a.nl; ++l) by += (double)sizeof(T) * P * a.m * a.K[l];
   c.kbegin();
   k_hexpand<T><<<grid, 256, 0, c.st>>>(a);
-  c.kend(KC_GEMM, fl, by);
+  c.kend(KC_HEXPAND, fl, by);
   c.gemm_flops += (long long)fl;
 }
 template void hexpand<float>(Ctx&, const HexpArgs<float>&, int);

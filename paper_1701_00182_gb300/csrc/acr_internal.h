@@ -199,7 +199,6 @@ template <class T> void copy2d(Ctx& c, int P, long rows, int cols, T alpha, cons
                                long sps, T* dst, long dld, long dps);
 template <class T> void set_identity_clusters(Ctx& c, int P, int m, int s, T* U, long ld, long ps);
 template <class T> int batched_inverse(Ctx& c, int nb, int n, T* A, long stride);  // in place GJ, returns 0
-template <class T> void build_coupling(Ctx& c, int P, int nodes, int K, const T* g, T* Mout);
 template <class T> void assemble_level0(Ctx& c, const Geometry& geo, const double* kappa, double shift,
                                         const int* d_perm, const int* d_iperm,
                                         const std::vector<const int*>& d_cutp,

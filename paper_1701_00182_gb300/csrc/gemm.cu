@@ -424,19 +424,21 @@ __global__ void k_scale_c(GArgs<T> g) {
 
 // ---- FP32 GEMM on the 5th-generation tensor cores (3xTF32) ---------------------
 // 128 x 128 output tile per CTA, accumulated in tensor memory (128 lanes x 128
-// FP32 columns).  Each 32-deep K slice of A and B is loaded by the 256 threads
-// (any strides, zero fill outside the operand), split into a TF32 high part
-// and the rounded remainder, and stored K-major in the 128-byte-swizzled
+// FP32 columns).  Each 32-deep K slice of A and B is loaded by the CTA's 512
+// threads (any strides, zero fill outside the operand), split into a TF32 high
+// part and the rounded remainder, and stored K-major in the 128-byte-swizzled
 // layout the tensor core reads (row r, 16-byte chunk q at r*128 + (q^(r%8))*16,
 // 8-row atoms 1 KB apart).  One thread then issues A_hi B_hi + A_hi B_lo +
 // A_lo B_hi as 3 x 4 MMAs of 128 x 128 x 8 and commits them to the slice's
 // mbarrier.  Three shared-memory stages and two register sets keep the global
-// loads of slices k+1 and k+2 in flight while the MMAs of slice k run.  The epilogue reads the accumulator with
-// tcgen05.ld (warp w: lanes 32 (w mod 4) .. +31, columns 64 (w / 4) .. +63).
-// Every mbarrier wait is bounded in time; on expiry the kernel sets an error
-// flag, skips its epilogue and still frees its tensor memory.
+// loads of slices k+1 and k+2 in flight while the MMAs of slice k run.  The
+// epilogue reads the accumulator with tcgen05.ld (warp w: lanes 32 (w mod 4)
+// .. +31, a quarter of the columns per w / 4).  Every mbarrier wait is bounded
+// in time; on expiry the kernel sets an error flag, skips its epilogue and
+// still frees its tensor memory.
 namespace tc {
 constexpr int BM = 128, BN = 128, BK = 32;
+constexpr int NT = 512;                      // 16 warps
 constexpr int TILE_BYTES = BM * BK * 4;      // 128 rows x 128 B
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A_hi, A_lo, B_hi, B_lo
 constexpr int NSTAGE = 3;
@@ -499,7 +501,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(256, 1) k_gemm_tc05(GArgs<float> g, int* err) {
+// AK: A(i, k) is contiguous along k (A.cs == 1); BKC: B(k, j) is contiguous
+// along k (B.rs == 1).  Lanes run along each operand's contiguous direction.
+template <bool AK, bool BKC>
+__global__ void __launch_bounds__(tc::NT, 1) k_gemm_tc05(GArgs<float> g, int* err) {
+  constexpr int QT = (tc::BM * tc::BK / 4) / tc::NT;  // quads of A (and of B) per thread per slice
   extern __shared__ unsigned char tc_raw[];
   __shared__ __align__(8) uint64_t bars[tc::NSTAGE];
   __shared__ uint32_t tmem_slot;
@@ -534,44 +540,49 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc05(GArgs<float> g, int* err) 
 
   const float* A = opaddr(g.A, plane, c);
   const float* B = opaddr(g.B, plane, c);
-  const long ars = g.A.rs, acs = g.A.cs, brs = g.B.rs, bcs = g.B.cs;
-  const bool a_kfast = (acs == 1), b_kfast = (brs == 1);
-  // Each thread owns 4 quads (4 consecutive k of one row) of A and of B per
-  // slice.  Lanes run along the contiguous global direction of the operand.
-  // Two register sets hold the slices k+1 and k+2 while slice k is stored.
-  float ra0[4][4], rb0[4][4], ra1[4][4], rb1[4][4];
+  const long ars = g.A.rs, acs = AK ? 1 : g.A.cs, brs = BKC ? 1 : g.B.rs, bcs = g.B.cs;
   // Fixed per thread for the whole K loop: the rows it loads, their first
   // element, whether they exist, and where their quads go in a stage.
-  const float* pa[4];
-  const float* pb[4];
-  bool va[4], vb[4];
-  int qa[4], qb[4];
-  uint32_t oa[4], ob[4];
+  float ra0[QT][4], rb0[QT][4], ra1[QT][4], rb1[QT][4];
+  const float* pa[QT];
+  const float* pb[QT];
+  bool va[QT], vb[QT];
+  int qa[QT], qb[QT];
+  uint32_t oa[QT], ob[QT];
 #pragma unroll
-  for (int it = 0; it < 4; ++it) {
-    const int e = tid + 256 * it;
-    int row = a_kfast ? (e >> 3) : (e & 127), q = a_kfast ? (e & 7) : (e >> 7);
+  for (int it = 0; it < QT; ++it) {
+    const int e = tid + tc::NT * it;
+    int row = AK ? (e >> 3) : (e & 127), q = AK ? (e & 7) : (e >> 7);
     va[it] = m0 + row < g.M;
     qa[it] = 4 * q;
     pa[it] = A + (long)(va[it] ? m0 + row : 0) * ars + (long)(kbeg + 4 * q) * acs;
     oa[it] = row * 128 + ((q ^ (row & 7)) << 4);
-    row = b_kfast ? (e >> 3) : (e & 127);
-    q = b_kfast ? (e & 7) : (e >> 7);
+    row = BKC ? (e >> 3) : (e & 127);
+    q = BKC ? (e & 7) : (e >> 7);
     vb[it] = n0 + row < g.N;
     qb[it] = 4 * q;
     pb[it] = B + (long)(vb[it] ? n0 + row : 0) * bcs + (long)(kbeg + 4 * q) * brs;
     ob[it] = row * 128 + ((q ^ (row & 7)) << 4);
   }
-  auto load = [&](int kc, float (&ra)[4][4], float (&rb)[4][4]) {
+  auto load = [&](int kc, float (&ra)[QT][4], float (&rb)[QT][4]) {
     const int kr = kend - kbeg - kc * tc::BK;  // k rows left in this slice (relative)
     const long ka = (long)kc * tc::BK * acs, kb = (long)kc * tc::BK * brs;
+    if (kr >= tc::BK) {
 #pragma unroll
-    for (int it = 0; it < 4; ++it) {
+      for (int it = 0; it < QT; ++it)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        ra[it][j] = (va[it] && qa[it] + j < kr) ? pa[it][ka + j * acs] : 0.f;
-        rb[it][j] = (vb[it] && qb[it] + j < kr) ? pb[it][kb + j * brs] : 0.f;
-      }
+        for (int j = 0; j < 4; ++j) {
+          ra[it][j] = va[it] ? pa[it][ka + j * acs] : 0.f;
+          rb[it][j] = vb[it] ? pb[it][kb + j * brs] : 0.f;
+        }
+    } else {
+#pragma unroll
+      for (int it = 0; it < QT; ++it)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          ra[it][j] = (va[it] && qa[it] + j < kr) ? pa[it][ka + j * acs] : 0.f;
+          rb[it][j] = (vb[it] && qb[it] + j < kr) ? pb[it][kb + j * brs] : 0.f;
+        }
     }
   };
   // TF32 high part rounded to nearest (ties away from zero: add half an ulp of
@@ -583,10 +594,10 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc05(GArgs<float> g, int* err) 
     h.z = hi(x[2]); l.z = hi(x[2] - h.z);
     h.w = hi(x[3]); l.w = hi(x[3] - h.w);
   };
-  auto store = [&](int s, const float (&ra)[4][4], const float (&rb)[4][4]) {
+  auto store = [&](int s, const float (&ra)[QT][4], const float (&rb)[QT][4]) {
     unsigned char* st = base + s * tc::STAGE_BYTES;
 #pragma unroll
-    for (int it = 0; it < 4; ++it) {
+    for (int it = 0; it < QT; ++it) {
       float4 h, l;
       split4(ra[it], h, l);
       *reinterpret_cast<float4*>(st + oa[it]) = h;
@@ -613,7 +624,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc05(GArgs<float> g, int* err) 
   // One step: wait until the MMAs that last read stage kc % NSTAGE are done,
   // store slice kc there, one barrier (which also votes on the waits), start
   // the loads of slice kc + 2 into the freed registers, issue the MMAs.
-  auto step = [&](int kc, float (&ra)[4][4], float (&rb)[4][4]) -> bool {
+  auto step = [&](int kc, float (&ra)[QT][4], float (&rb)[QT][4]) -> bool {
     const int s = kc % tc::NSTAGE;
     bool ok = true;
     if (kc >= tc::NSTAGE) ok = mbar_wait_bounded(smem_u32(&bars[s]), ((kc - tc::NSTAGE) / tc::NSTAGE) & 1);
@@ -637,10 +648,12 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc05(GArgs<float> g, int* err) 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (s_ok) {
-    const int lb = (warp & 3) * 32, cb = (warp >> 2) * 64;
+    // warp w reads TMEM lanes 32 (w mod 4) .. +31 and columns CW (w / 4) .. +CW-1
+    constexpr int CW = tc::BN / (tc::NT / 128);
+    const int lb = (warp & 3) * 32, cb = (warp >> 2) * CW;
     const int gi = m0 + lb + lane;
 #pragma unroll 1
-    for (int ch = 0; ch < 4; ++ch) {
+    for (int ch = 0; ch < CW / 16; ++ch) {
       uint32_t r[16];
       if (nk > 0) {
         tmem_ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)(cb + ch * 16), r);
@@ -678,6 +691,20 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc05(GArgs<float> g, int* err) 
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::TMEM_COLS));
 }
 
+template <bool AK, bool BKC>
+void launch_tc05(dim3 grid, const GArgs<float>& g, cudaStream_t st, int* err) {
+  ACR_CUDA(cudaFuncSetAttribute(k_gemm_tc05<AK, BKC>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+  k_gemm_tc05<AK, BKC><<<grid, tc::NT, tc::SMEM_BYTES, st>>>(g, err);
+}
+
+void launch_tc05_any(dim3 grid, const GArgs<float>& g, cudaStream_t st, int* err) {
+  const bool ak = g.A.cs == 1, bk = g.B.rs == 1;
+  if (ak && bk) launch_tc05<true, true>(grid, g, st, err);
+  else if (ak) launch_tc05<true, false>(grid, g, st, err);
+  else if (bk) launch_tc05<false, true>(grid, g, st, err);
+  else launch_tc05<false, false>(grid, g, st, err);
+}
+
 namespace {
 
 struct Cfg {
@@ -707,8 +734,7 @@ void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st, int* err
       break;
     default:
       if constexpr (sizeof(T) == 4) {
-        ACR_CUDA(cudaFuncSetAttribute(k_gemm_tc05, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
-        k_gemm_tc05<<<grid, 256, tc::SMEM_BYTES, st>>>(g, err);
+        launch_tc05_any(grid, g, st, err);
       } else {
         k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g);
       }

@@ -140,6 +140,34 @@ void wsum_apply(Ctx& c, const WSum<T>& X, int lmin, bool trans, Pan<T> W, Pan<T>
 }
 
 // Recursive-Woodbury inverse of the P HODLR matrices D (any plane stride).
+// Inverses of all Woodbury couplings of one level, stored row-block-swapped
+// (the operator applied to the stacked child coefficients):
+//   M'_t = [[g1, I], [I, g2]],  g1 = g(2t), g2 = g(2t+1)  (K x K each).
+// Block elimination: M'^{-1} = [[-g2 S, T], [S, -g1 T]] with S = (I - g1 g2)^{-1}
+// and T = (I - g2 g1)^{-1} = I + g2 S g1 (push-through identity), so one
+// pivoted inverse of order K and four batched products replace the inverse
+// of order 2K (8x fewer pivoting flops; the products run on the GEMM path).
+template <class T>
+void coupling_inverse(Ctx& c, int P, int nodes, int K, T* g, T* Kp) {
+  const long KK = (long)K * K, K2 = 2L * K, blk = 4L * KK;
+  const long gps = 2L * nodes * KK;  // g: [P][2 nodes][K][K]
+  const long bps = (long)nodes * blk;
+  DBuf<T> S(c, (size_t)P * nodes * KK);
+  set_identity_clusters<T>(c, P * nodes, K, K, S.p, K, KK);
+  c.tag = "inv_schur";
+  gemm<T>(c, K, K, K, P, nodes, T(-1), opm<T>(g, K, 1, gps, 2 * KK), opm<T>(g + KK, K, 1, gps, 2 * KK), T(1),
+          opm<T>(S.p, K, 1, (long)nodes * KK, KK));
+  batched_inverse<T>(c, P * nodes, K, S.p, KK);
+  gemm<T>(c, K, K, K, P, nodes, T(-1), opm<T>(g + KK, K, 1, gps, 2 * KK), opm<T>(S.p, K, 1, (long)nodes * KK, KK),
+          T(0), opm<T>(Kp, K2, 1, bps, blk));
+  copy2d<T>(c, P * nodes, K, K, T(1), S.p, K, KK, Kp + K2 * K, K2, blk);
+  set_identity_clusters<T>(c, P * nodes, K, K, Kp + K, K2, blk);
+  gemm<T>(c, K, K, K, P, nodes, T(-1), opm<T>(Kp, K2, 1, bps, blk), opm<T>(g, K, 1, gps, 2 * KK), T(1),
+          opm<T>(Kp + K, K2, 1, bps, blk));
+  gemm<T>(c, K, K, K, P, nodes, T(-1), opm<T>(g, K, 1, gps, 2 * KK), opm<T>(Kp + K, K2, 1, bps, blk), T(0),
+          opm<T>(Kp + K2 * K + K, K2, 1, bps, blk));
+}
+
 template <class T>
 WSum<T> winverse(Ctx& c, const HMat<T>& D) {
   WSum<T> X;
@@ -163,8 +191,7 @@ WSum<T> winverse(Ctx& c, const HMat<T>& D) {
             opm<T>(X.Pc[l].p, K, 1, (long)m * K, (long)s * K), T(0),
             opm<T>(g.p, K, 1, (long)nclus * K * K, (long)K * K));
     X.Kp[l] = DBuf<T>(c, (size_t)P * nodes * 4 * K * K);
-    build_coupling<T>(c, P, nodes, K, g.p, X.Kp[l].p);
-    batched_inverse<T>(c, P * nodes, 2 * K, X.Kp[l].p, 4L * K * K);
+    coupling_inverse<T>(c, P, nodes, K, g.p, X.Kp[l].p);
     X.have[l] = true;
   }
   return X;

@@ -207,34 +207,6 @@ int batched_inverse(Ctx& c, int nb, int n, T* A, long stride) {
   return 0;
 }
 
-// Woodbury coupling of node t at one level, rows swapped so that its inverse
-// is directly the operator applied to the stacked child coefficients:
-//   M'_t = [[g(2t), I], [I, g(2t+1)]],  g(c) = V|c^T (X U)|c  (K x K).
-template <class T>
-__global__ void k_build_coupling(int P, int nodes, int K, const T* g, T* M) {
-  long K2 = 2L * K;
-  long tot = (long)P * nodes * K2 * K2;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
-    long nt = e / (K2 * K2);
-    long r = e - nt * K2 * K2;
-    int i = (int)(r / K2), j = (int)(r % K2);
-    int a = i >= K, b = j >= K;
-    int ii = i - a * K, jj = j - b * K;
-    T v;
-    if (a == b) v = g[((nt * 2 + a) * K + ii) * (long)K + jj];
-    else v = (ii == jj) ? T(1) : T(0);
-    M[e] = v;
-  }
-}
-template <class T>
-void build_coupling(Ctx& c, int P, int nodes, int K, const T* g, T* Mout) {
-  long tot = (long)P * nodes * 4L * K * K;
-  if (tot <= 0) return;
-  c.kbegin();
-  k_build_coupling<T><<<nblk(tot), 256, 0, c.st>>>(P, nodes, K, g, Mout);
-  c.kend(KC_COPY, 0, (double)sizeof(T) * tot);
-}
-
 // ---- level-0 assembly --------------------------------------------------------
 
 __device__ __forceinline__ double harm(double a, double b, double ih2) { return 2.0 * a * b / (a + b) * ih2; }
@@ -654,7 +626,6 @@ void exp_inplace(Ctx& c, double* p, long n) {
   template void copy2d<T>(Ctx&, int, long, int, T, const T*, long, long, T*, long, long);                \
   template void set_identity_clusters<T>(Ctx&, int, int, int, T*, long, long);                           \
   template int batched_inverse<T>(Ctx&, int, int, T*, long);                                             \
-  template void build_coupling<T>(Ctx&, int, int, int, const T*, T*);                                    \
   template void assemble_level0<T>(Ctx&, const Geometry&, const double*, double, const int*, const int*, \
                                    const std::vector<const int*>&, const std::vector<const int*>&,       \
                                    HMat<T>, HMat<T>, HMat<T>);                                           \

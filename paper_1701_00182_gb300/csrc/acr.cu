@@ -54,7 +54,7 @@ void Ctx::kbegin() {
   ACR_CUDA(cudaEventRecord(evcur, st));
 }
 
-void Ctx::kend(int cls, double flops, double bytes) {
+void Ctx::kend(int cls, double flops, double bytes, const char* name) {
   ++launches;
   kc_launch[cls] += 1;
   kc_flops[cls] += flops;
@@ -69,8 +69,9 @@ void Ctx::kend(int cls, double flops, double bytes) {
   evfree.pop_back();
   ACR_CUDA(cudaEventRecord(b, st));
   const bool g = cls == KC_GEMM || cls == KC_GEMM_TC || cls == KC_HEXPAND;
-  pend.push_back({evcur, b, cls, g ? tag : nullptr});
-  if (g) site[tag].second += flops;
+  const char* key = g ? tag : (site_detail ? name : nullptr);
+  pend.push_back({evcur, b, cls, key});
+  if (key) site[key].second += g ? flops : bytes;
   evcur = nullptr;
   if (pend.size() >= 8192) kflush();
 }

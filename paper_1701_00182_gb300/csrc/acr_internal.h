@@ -73,7 +73,8 @@ struct Ctx {
   std::vector<PendingEv> pend;
   cudaEvent_t evcur = nullptr;
   void kbegin();
-  void kend(int cls, double flops, double bytes);
+  // name: label of a non-GEMM launch in the per-site profile (ACR_PROFILE_SITES=2; its bytes are recorded)
+  void kend(int cls, double flops, double bytes, const char* name = nullptr);
   void kflush();
   void* dalloc_bytes(size_t bytes);
   void dfree(void* p, size_t bytes);
@@ -114,9 +115,11 @@ template <class T>
 void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta,
           Op<T> C);
 
-// C = alpha * A B + beta * C for symmetric C (M x M, A = B^T): upper triangle computed, then mirrored.
+// C = alpha * A B + beta * C for symmetric C (M x M, A = B^T): the upper triangle is computed, then
+// mirrored; with mirror = false the entries below the diagonal are left unspecified.
 template <class T>
-void gemm_sym(Ctx& c, int M, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta, Op<T> C);
+void gemm_sym(Ctx& c, int M, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta, Op<T> C,
+              bool mirror = true);
 
 // Fused HODLR x panel expansion (leaf product + every level's expansion).
 template <class T>

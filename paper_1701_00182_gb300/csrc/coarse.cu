@@ -155,7 +155,7 @@ void convert(Ctx& c, long n, const S* a, D* b) {
   if (n <= 0) return;
   c.kbegin();
   k_cvt<S, D><<<nblk(n), 256, 0, c.st>>>(n, a, b);
-  c.kend(KC_COPY, 0, (double)(sizeof(S) + sizeof(D)) * n);
+  c.kend(KC_COPY, 0, (double)(sizeof(S) + sizeof(D)) * n, "copy:convert");
 }
 
 template void convert<float, double>(Ctx&, long, const float*, double*);

@@ -23,7 +23,7 @@ struct GArgs {
   Op<T> A, B, C;
   int kchunk;
   T* partial;
-  int sym;  // C is symmetric (A = B^T): only tiles touching the upper triangle are computed
+  int sym;  // C is symmetric (A = B^T): only tiles touching the upper triangle are computed (2: no mirror pass)
 };
 
 template <class T>
@@ -841,7 +841,7 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
     int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
     c.kbegin();
     k_scale_c<T><<<nb, 256, 0, c.st>>>(g);
-    c.kend(KC_COPY, 0, 2.0 * sizeof(T) * tot);
+    c.kend(KC_COPY, 0, 2.0 * sizeof(T) * tot, "copy:scale_c");
     return;
   }
   if (batch > 0x7fffffffL) throw AcrError(1, "gemm batch too large");
@@ -903,12 +903,12 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
     c.tag = c.tagstore.insert(buf).first->c_str();
   }
   run_gemm<T>(c, cfg, split, M, N, K, batch, g);
-  if (sym) {
+  if (sym == 1) {
     long tot = batch * (long)M * N;
     int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
     c.kbegin();
     k_mirror<T><<<nb, 256, 0, c.st>>>(g);
-    c.kend(KC_COPY, 0, (double)sizeof(T) * tot);
+    c.kend(KC_COPY, 0, (double)sizeof(T) * tot, "copy:mirror");
   }
 }
 
@@ -918,8 +918,8 @@ void gemm(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alpha, Op<T> A,
 }
 
 template <class T>
-void gemm_sym(Ctx& c, int M, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta, Op<T> C) {
-  gemm_impl<T>(c, M, M, K, nplanes, nclus, alpha, A, B, beta, C, 1);
+void gemm_sym(Ctx& c, int M, int K, int nplanes, int nclus, T alpha, Op<T> A, Op<T> B, T beta, Op<T> C, bool mirror) {
+  gemm_impl<T>(c, M, M, K, nplanes, nclus, alpha, A, B, beta, C, mirror ? 1 : 2);
 }
 
 // ---- fused multi-level expansion of a HODLR x panel product -------------------
@@ -1033,8 +1033,8 @@ void hexpand(Ctx& c, const HexpArgs<T>& a, int P) {
 template void hexpand<float>(Ctx&, const HexpArgs<float>&, int);
 template void hexpand<double>(Ctx&, const HexpArgs<double>&, int);
 
-template void gemm_sym<float>(Ctx&, int, int, int, int, float, Op<float>, Op<float>, float, Op<float>);
-template void gemm_sym<double>(Ctx&, int, int, int, int, double, Op<double>, Op<double>, double, Op<double>);
+template void gemm_sym<float>(Ctx&, int, int, int, int, float, Op<float>, Op<float>, float, Op<float>, bool);
+template void gemm_sym<double>(Ctx&, int, int, int, int, double, Op<double>, Op<double>, double, Op<double>, bool);
 template void gemm<float>(Ctx&, int, int, int, int, int, float, Op<float>, Op<float>, float, Op<float>);
 template void gemm<double>(Ctx&, int, int, int, int, int, double, Op<double>, Op<double>, double,
                            Op<double>);

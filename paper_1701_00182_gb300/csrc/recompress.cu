@@ -132,27 +132,55 @@ __global__ void __launch_bounds__(256) k_qr_small(int s, int r, int nclus, long 
 // term, so the pivoted Cholesky thresholds below compare terms by their
 // contribution to M.  Columns with a zero partner are dropped (a = 0).
 template <class T>
-__global__ void k_balance(int r, long NB, T* G, T* aL, T* aR) {
-  const long bi = blockIdx.x;
-  T* GL = G + bi * (long)r * r;
-  T* GR = G + (NB + bi) * (long)r * r;
-  T* al = aL + bi * r;
-  T* ar = aR + bi * r;
-  for (int j = threadIdx.x; j < r; j += blockDim.x) {
-    T nl = sqrt(fmax(GL[(long)j * r + j], T(0))), nr = sqrt(fmax(GR[(long)j * r + j], T(0)));
+__global__ void k_balance_scales(int r, long NB, const T* G, T* aL, T* aR) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < NB * r; e += (long)gridDim.x * blockDim.x) {
+    const long bi = e / r;
+    const int j = (int)(e - bi * r);
+    const T gl = G[(bi * r + j) * (long)r + j], gr = G[((NB + bi) * r + j) * (long)r + j];
+    const T nl = sqrt(fmax(gl, T(0))), nr = sqrt(fmax(gr, T(0)));
     T a = T(0), b = T(0);
     if (nl > T(0) && nr > T(0)) {
       a = sqrt(nr / nl);
       b = T(1) / a;
     }
-    al[j] = a;
-    ar[j] = b;
+    aL[e] = a;
+    aR[e] = b;
   }
-  __syncthreads();
-  for (long e = threadIdx.x; e < (long)r * r; e += blockDim.x) {
-    int i = (int)(e / r), j = (int)(e % r);
-    GL[e] *= al[i] * al[j];
-    GR[e] *= ar[i] * ar[j];
+}
+
+// The Gram GEMM fills only the upper triangle (i <= j).  One CTA per pair of
+// 32 x 32 tiles (ti <= tj) of one matrix reads the upper tile once and writes
+// it and its mirror image, both scaled by a_i a_j, so every element of the
+// full symmetric result is written exactly once from unscaled data.
+template <class T>
+__global__ void __launch_bounds__(256) k_mirror_scale(int r, long NB, T* G, const T* aL, const T* aR) {
+  __shared__ T t[32][33];
+  const long z = blockIdx.x;  // matrix: side = z / NB, block z % NB
+  const int nt = (r + 31) / 32;
+  T* M = G + z * (long)r * r;
+  const T* a = (z < NB) ? aL + z * r : aR + (z - NB) * r;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int pr = blockIdx.y; pr < nt * nt; pr += gridDim.y) {
+    const int ti = pr / nt, tj = pr % nt;
+    if (ti > tj) continue;  // uniform over the CTA
+    const int i0 = ti * 32, j0 = tj * 32;
+    for (int ii = ty; ii < 32; ii += 8) {
+      const int i = i0 + ii, j = j0 + tx;
+      t[ii][tx] = (i < r && j < r && (ti < tj || ii <= tx)) ? M[(long)i * r + j] : T(0);
+    }
+    __syncthreads();
+    for (int ii = ty; ii < 32; ii += 8) {
+      const int i = i0 + ii, j = j0 + tx;
+      if (i < r && j < r) {
+        const T v = (ti < tj || ii <= tx) ? t[ii][tx] : t[tx][ii];
+        M[(long)i * r + j] = v * a[i] * a[j];
+      }
+      if (ti < tj) {  // mirror tile (tj, ti): row j0 + ii, column i0 + tx
+        const int mi = j0 + ii, mj = i0 + tx;
+        if (mi < r && mj < r) M[(long)mi * r + mj] = t[tx][ii] * a[mi] * a[mj];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -760,12 +788,17 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
       Op<T> B{F, r, 1, (long)m * r, (long)s * r, 0, 0, side};
       Op<T> C{G.p + side * NB * r * (long)r, r, 1, (long)nclus * r * r, (long)r * r, 0, 0, 0};
       c.tag = "gram";
-      gemm_sym<T>(c, r, s, P, nclus, T(1), A, B, T(0), C);
+      gemm_sym<T>(c, r, s, P, nclus, T(1), A, B, T(0), C, false);
     }
     scale = DBuf<T>(c, 2 * NB * (size_t)r);
     c.kbegin();
-    k_balance<T><<<(unsigned)NB, 256, 0, c.st>>>(r, NB, G.p, scale.p, scale.p + NB * r);
-    c.kend(KC_COPY, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r);
+    k_balance_scales<T><<<(unsigned)std::min<long>((NB * r + 255) / 256, 152L * 16), 256, 0, c.st>>>(
+        r, NB, G.p, scale.p, scale.p + NB * r);
+    const int nt = (r + 31) / 32;
+    k_mirror_scale<T><<<dim3((unsigned)(2 * NB), (unsigned)std::min(nt * nt, 65535)), 256, 0, c.st>>>(
+        r, NB, G.p, scale.p, scale.p + NB * r);
+    c.kend(KC_COPY, 0, 2.0 * NB * sizeof(T) * 1.5 * r * r, "copy:balance");
+    c.launches += 1;
     double epsd = std::max(0.01 * tol * tol, sizeof(T) == 8 ? 1e-15 : 1e-5);
     size_t sm = 2 * (size_t)r * sizeof(T);
     if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_pchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));

@@ -25,20 +25,22 @@ void fill(Ctx& c, T* p, long n, T v) {
   if (n <= 0) return;
   c.kbegin();
   k_fill<T><<<nblk(n), 256, 0, c.st>>>(p, n, v);
-  c.kend(KC_COPY, 0, (double)sizeof(T) * n);
+  c.kend(KC_COPY, 0, (double)sizeof(T) * n, "copy:fill");
 }
 
-// dst[p][row][j] = alpha * src[p][row][j], j < cols.
+// dst[p][row][j] = alpha * src[p][row][j], j < cols.  One warp per row (lanes
+// along the row), so the index division happens once per row.
 template <class T>
 __global__ void k_copy2d(int P, long rows, int cols, T alpha, const T* src, long sld, long sps, T* dst,
                          long dld, long dps) {
-  long tot = (long)P * rows * cols;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
-    long p = e / (rows * cols);
-    long r = e - p * rows * cols;
-    long i = r / cols;
-    int j = (int)(r - i * cols);
-    dst[p * dps + i * dld + j] = alpha * src[p * sps + i * sld + j];
+  const long nrow = (long)P * rows;
+  const int lane = threadIdx.x & 31;
+  for (long rw = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; rw < nrow;
+       rw += ((long)gridDim.x * blockDim.x) >> 5) {
+    const long p = rw / rows, i = rw - p * rows;
+    const T* sr = src + p * sps + i * sld;
+    T* dr = dst + p * dps + i * dld;
+    for (int j = lane; j < cols; j += 32) dr[j] = alpha * sr[j];
   }
 }
 template <class T>
@@ -51,8 +53,8 @@ void copy2d(Ctx& c, int P, long rows, int cols, T alpha, const T* src, long sld,
     c.check_range(dst, 0, (long)(P - 1) * dps + (rows - 1) * dld + cols - 1, sizeof(T), "copy2d dst");
   }
   c.kbegin();
-  k_copy2d<T><<<nblk(tot), 256, 0, c.st>>>(P, rows, cols, alpha, src, sld, sps, dst, dld, dps);
-  c.kend(KC_COPY, 0, 2.0 * sizeof(T) * tot);
+  k_copy2d<T><<<nblk((long)P * rows * 32), 256, 0, c.st>>>(P, rows, cols, alpha, src, sld, sps, dst, dld, dps);
+  c.kend(KC_COPY, 0, 2.0 * sizeof(T) * tot, "copy:copy2d");
 }
 
 // Every cluster (size s) of every plane: U|c = I_s  (panel of width s).
@@ -73,7 +75,7 @@ void set_identity_clusters(Ctx& c, int P, int m, int s, T* U, long ld, long ps) 
   if (tot <= 0) return;
   c.kbegin();
   k_identity<T><<<nblk(tot), 256, 0, c.st>>>(P, m, s, U, ld, ps);
-  c.kend(KC_COPY, 0, (double)sizeof(T) * tot);
+  c.kend(KC_COPY, 0, (double)sizeof(T) * tot, "copy:identity");
 }
 
 // In-place Gauss-Jordan inversion with partial (row) pivoting, one CTA per
@@ -189,11 +191,11 @@ int batched_inverse(Ctx& c, int nb, int n, T* A, long stride) {
     double* Ad = c.alloc<double>(tot);
     c.kbegin();
     k_convert<T, double><<<nblk(tot), 256, 0, c.st>>>(tot, A, Ad);
-    c.kend(KC_COPY, 0, 12.0 * tot);
+    c.kend(KC_COPY, 0, 12.0 * tot, "copy:inv_fp64");
     batched_inverse<double>(c, nb, n, Ad, stride);
     c.kbegin();
     k_convert<double, T><<<nblk(tot), 256, 0, c.st>>>(tot, Ad, A);
-    c.kend(KC_COPY, 0, 12.0 * tot);
+    c.kend(KC_COPY, 0, 12.0 * tot, "copy:inv_fp64");
     c.free(Ad, tot);
     return 0;
   }
@@ -539,7 +541,7 @@ void col_dots(Ctx& c, long N, int nrhs, const double* x, long ldx, const double*
   c.kend(KC_STENCIL, 0, 16.0 * nb * nrhs);
   c.kbegin();
   k_copy2d<double><<<1, 64, 0, c.st>>>(1, nrhs, 1, 1.0, pairs, 2, 0, out, 1, 0);
-  c.kend(KC_COPY, 0, 16.0 * nrhs);
+  c.kend(KC_COPY, 0, 16.0 * nrhs, "copy:norms");
   c.free(part, (size_t)nb * nrhs * 2);
   c.free(pairs, (size_t)nrhs * 2);
 }
@@ -567,17 +569,18 @@ void col_scale_copy(Ctx& c, long N, int nrhs, const double* a, const double* x, 
 }
 
 
-// dst[p][row][j] += alpha * src[p][row][j], j < cols.
+// dst[p][row][j] += alpha * src[p][row][j], j < cols (one warp per row).
 template <class T>
 __global__ void k_axpy2d(int P, long rows, int cols, T alpha, const T* src, long sld, long sps, T* dst, long dld,
                          long dps) {
-  long tot = (long)P * rows * cols;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
-    long p = e / (rows * cols);
-    long r = e - p * rows * cols;
-    long i = r / cols;
-    int j = (int)(r - i * cols);
-    dst[p * dps + i * dld + j] += alpha * src[p * sps + i * sld + j];
+  const long nrow = (long)P * rows;
+  const int lane = threadIdx.x & 31;
+  for (long rw = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; rw < nrow;
+       rw += ((long)gridDim.x * blockDim.x) >> 5) {
+    const long p = rw / rows, i = rw - p * rows;
+    const T* sr = src + p * sps + i * sld;
+    T* dr = dst + p * dps + i * dld;
+    for (int j = lane; j < cols; j += 32) dr[j] += alpha * sr[j];
   }
 }
 template <class T>
@@ -590,8 +593,8 @@ void axpy2d(Ctx& c, int P, long rows, int cols, T alpha, const T* src, long sld,
     c.check_range(dst, 0, (long)(P - 1) * dps + (rows - 1) * dld + cols - 1, sizeof(T), "axpy2d dst");
   }
   c.kbegin();
-  k_axpy2d<T><<<nblk(tot), 256, 0, c.st>>>(P, rows, cols, alpha, src, sld, sps, dst, dld, dps);
-  c.kend(KC_COPY, 0, 3.0 * sizeof(T) * tot);
+  k_axpy2d<T><<<nblk((long)P * rows * 32), 256, 0, c.st>>>(P, rows, cols, alpha, src, sld, sps, dst, dld, dps);
+  c.kend(KC_COPY, 0, 3.0 * sizeof(T) * tot, "copy:axpy2d");
 }
 
 // Dense m x m image of the leaf blocks of one HODLR matrix (off-diagonal zero).
@@ -609,7 +612,7 @@ template <class T>
 void expand_leaves(Ctx& c, int m, int b, const T* leaf, T* dense) {
   c.kbegin();
   k_expand_leaves<T><<<nblk((long)m * b), 256, 0, c.st>>>(m, b, leaf, dense);
-  c.kend(KC_COPY, 0, 2.0 * sizeof(T) * (double)m * b);
+  c.kend(KC_COPY, 0, 2.0 * sizeof(T) * (double)m * b, "copy:expand_leaves");
 }
 
 __global__ void k_exp_inplace(double* p, long n) {

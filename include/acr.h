@@ -94,7 +94,8 @@ typedef struct {
    * 0 batched GEMM (CUDA-core and mma.sync tilings), 1 split-K reduction, 2 Householder QR, 3 pivoted Cholesky, 4 core truncation (Jacobi SVD or pivoted QR),
    * 5 rebuild coefficients, 6 Gauss-Jordan inverse, 7 copies/fills, 8 assembly, 9 RHS permutation,
    * 10 FP64 stencil and column reductions, 11 FP32 GEMM tiles on the tcgen05 tensor cores (3xTF32),
-   * 12 fused HODLR x panel expansion.  flops/bytes are algorithmic counts (each operand once). */
+   * 12 fused HODLR x panel expansion, 13 TF32 high/remainder split of GEMM operands into TMA tiles.
+   * flops/bytes are algorithmic counts (each operand once). */
   double kc_ms[16];
   double kc_flops[16];
   double kc_bytes[16];

@@ -31,7 +31,8 @@ ACR_ERR_NOT_CONVERGED = 6
 ACR_FP64 = 0
 ACR_FP32 = 1
 KERNEL_CLASSES = ("gemm", "splitk_reduce", "householder_qr", "pivoted_cholesky", "core_truncation", "rebuild_coef",
-                  "gauss_jordan", "copy", "assemble", "permute", "stencil_fp64", "gemm_tcgen05", "hodlr_expand")
+                  "gauss_jordan", "copy", "assemble", "permute", "stencil_fp64", "gemm_tcgen05", "hodlr_expand",
+                  "tf32_split")
 
 
 class AcrOpts(C.Structure):

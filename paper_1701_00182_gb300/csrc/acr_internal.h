@@ -42,7 +42,7 @@ struct AcrError : std::runtime_error {
 
 // Kernel classes for the per-class profile (CUDA events on the launch stream).
 enum KClass { KC_GEMM, KC_SPLITK, KC_QR, KC_PCHOL, KC_JACOBI, KC_COEF, KC_GJ, KC_COPY, KC_ASSEMBLE, KC_PERMUTE,
-              KC_STENCIL, KC_GEMM_TC, KC_HEXPAND, KC_N };
+              KC_STENCIL, KC_GEMM_TC, KC_HEXPAND, KC_TF32SPLIT, KC_N };
 
 // Execution context of one handle: stream, scratch, counters, autotune cache.
 struct Ctx {

@@ -13,24 +13,9 @@
 #include <mutex>
 
 #include "acr_internal.h"
+#include "tc_common.cuh"
 
 namespace acr {
-
-template <class T>
-struct GArgs {
-  int M, N, K, nclus, batch;
-  T alpha, beta;
-  Op<T> A, B, C;
-  int kchunk;
-  T* partial;
-  int sym;  // C is symmetric (A = B^T): only tiles touching the upper triangle are computed (2: no mirror pass)
-};
-
-template <class T>
-__device__ __forceinline__ T* opaddr(const Op<T>& o, int plane, int c) {
-  int cc = o.sib ? (c ^ 1) : c;
-  return o.p + (long)plane * o.ps + (long)(cc >> o.sh) * o.c1 + (long)(cc & 1) * o.c2;
-}
 
 template <class T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GArgs<T> g) {
@@ -444,62 +429,9 @@ constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A_hi, A_lo, B_hi, B_lo
 constexpr int NSTAGE = 3;
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;  // + slack for the 1 KB alignment
 constexpr uint32_t TMEM_COLS = 128;
-constexpr unsigned long long WAIT_NS = 2000000000ull;
 // instruction descriptor: D F32, A and B TF32, both K-major, N >> 3, M >> 4
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }  // namespace tc
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Shared-memory matrix descriptor: start address, leading byte offset 16 (not
-// used by a swizzled K-major operand), stride byte offset 1024 (next 8-row
-// atom), descriptor version 1, 128-byte swizzle.
-__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ void umma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  unsigned long long t0 = 0;
-  for (int it = 0;; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (it == 0) t0 = global_ns();
-    else if ((it & 31) == 0 && global_ns() - t0 > tc::WAIT_NS) return false;
-  }
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 // AK: A(i, k) is contiguous along k (A.cs == 1); BKC: B(k, j) is contiguous
 // along k (B.rs == 1).  Lanes run along each operand's contiguous direction.
@@ -710,11 +642,12 @@ namespace {
 struct Cfg {
   int bm, bn, bk;
 };
-constexpr int kNCfg = 7;
-constexpr Cfg kCfg[kNCfg] = {{64, 64, 16},   {128, 64, 8},   {32, 32, 32},  {128, 128, 8},
-                             {128, 128, 8}, {128, 128, 16}, {128, 128, 32}};
+constexpr int kNCfg = 8;
+constexpr Cfg kCfg[kNCfg] = {{64, 64, 16},   {128, 64, 8},   {32, 32, 32},   {128, 128, 8},
+                             {128, 128, 8}, {128, 128, 16}, {128, 128, 32}, {128, 128, 32}};
 
-// Configurations 5 (mma.sync 3xTF32) and 6 (tcgen05 3xTF32) exist for FP32 only.
+// Configurations 5 (mma.sync 3xTF32), 6 (tcgen05 3xTF32, in-kernel split) and
+// 7 (tcgen05 3xTF32, pre-split tiles fed by TMA) exist for FP32 only.
 bool cfg_valid(int cfg, int es, bool tensor) { return cfg < 5 || (tensor && es == 4); }
 
 template <class T>
@@ -742,8 +675,8 @@ void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st, int* err
   }
 }
 
-int heuristic_cfg(int M, int N, long batch, int es, bool tensor) {
-  if (es == 4 && tensor && M >= 64 && N >= 32) return 6;
+int heuristic_cfg(int M, int N, int K, long batch, int es, bool tensor) {
+  if (es == 4 && tensor && M >= 64 && N >= 32) return (M >= 512 && N >= 512 && K >= 512) ? 7 : 6;
   if (M <= 32 && N <= 32) return 2;
   if (M >= 96 && N >= 96) return es == 4 ? (tensor ? 6 : 4) : 3;
   if (M >= 128 && N <= 64) return 1;
@@ -782,9 +715,13 @@ static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch
     g.kchunk = kchunk;
     g.partial = part;
     const double es = sizeof(T);
-    c.kbegin();
-    launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, split), g, c.st, c.d_flag + 2);
-    c.kend(cls, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch, es * batch * ((double)M * K + (double)K * N + (double)M * N * split));
+    if (cfg == 7) {
+      if constexpr (sizeof(T) == 4) gemm_tma(c, g, batch, split, c.d_flag + 2);
+    } else {
+      c.kbegin();
+      launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, split), g, c.st, c.d_flag + 2);
+      c.kend(cls, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch, es * batch * ((double)M * K + (double)K * N + (double)M * N * split));
+    }
     long tot = batch * (long)M * N;
     int nb = (int)std::min<long>((tot + 255) / 256, 152L * 16);
     c.kbegin();
@@ -794,10 +731,14 @@ static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch
   } else {
     g.kchunk = K;
     g.partial = nullptr;
-    c.kbegin();
-    launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, 1), g, c.st, c.d_flag + 2);
-    c.kend(cls, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch,
-           (double)sizeof(T) * batch * ((double)M * K + (double)K * N + (double)M * N * (1 + (g.beta != T(0)))));
+    if (cfg == 7) {
+      if constexpr (sizeof(T) == 4) gemm_tma(c, g, batch, 1, c.d_flag + 2);
+    } else {
+      c.kbegin();
+      launch_cfg<T>(cfg, dim3((unsigned)batch, tiles, 1), g, c.st, c.d_flag + 2);
+      c.kend(cls, (g.sym ? 1.0 * M * (N + 1) : 2.0 * M * N) * K * batch,
+             (double)sizeof(T) * batch * ((double)M * K + (double)K * N + (double)M * N * (1 + (g.beta != T(0)))));
+    }
   }
 }
 
@@ -847,7 +788,7 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
   if (batch > 0x7fffffffL) throw AcrError(1, "gemm batch too large");
   c.gemm_flops += (sym ? 1LL * M * (N + 1) : 2LL * M * N) * K * batch;
   GArgs<T> g{M, N, K, nclus, (int)batch, alpha, beta, A, B, C, K, nullptr, sym};
-  int cfg = heuristic_cfg(M, N, batch, (int)sizeof(T), c.tensor);
+  int cfg = heuristic_cfg(M, N, K, batch, (int)sizeof(T), c.tensor);
   int split = split_for(cfg, M, N, K, batch);
   if (c.force_cfg >= 0 && c.force_cfg < kNCfg && cfg_valid(c.force_cfg, (int)sizeof(T), c.tensor)) {
     cfg = c.force_cfg;

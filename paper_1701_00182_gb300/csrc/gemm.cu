@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(tc::NT, 1) k_gemm_tc05(GArgs<float> g, int* er
     // warp w reads TMEM lanes 32 (w mod 4) .. +31 and columns CW (w / 4) .. +CW-1
     constexpr int CW = tc::BN / (tc::NT / 128);
     const int lb = (warp & 3) * 32, cb = (warp >> 2) * CW;
-    const int gi = m0 + lb + lane;
+    float* stg = reinterpret_cast<float*>(base) + warp * 32 * 17;  // stages are free now
 #pragma unroll 1
     for (int ch = 0; ch < CW / 16; ++ch) {
       uint32_t r[16];
@@ -593,27 +593,7 @@ __global__ void __launch_bounds__(tc::NT, 1) k_gemm_tc05(GArgs<float> g, int* er
 #pragma unroll
         for (int j = 0; j < 16; ++j) r[j] = 0u;
       }
-      if (gi < g.M) {
-        if (g.partial) {
-          float* P = g.partial + ((long)blockIdx.z * g.batch + bi) * (long)g.M * g.N + (long)gi * g.N;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int gj = n0 + cb + ch * 16 + j;
-            if (gj < g.N) P[gj] = __uint_as_float(r[j]);
-          }
-        } else {
-          float* C = opaddr(g.C, plane, c) + (long)gi * g.C.rs;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int gj = n0 + cb + ch * 16 + j;
-            if (gj >= g.N) continue;
-            float* cp = C + (long)gj * g.C.cs;
-            float v = g.alpha * __uint_as_float(r[j]);
-            if (g.beta != 0.f) v += g.beta * *cp;
-            *cp = v;
-          }
-        }
-      }
+      store_chunk(g, stg, r, lane, m0 + lb, n0 + cb + ch * 16, plane, c, bi);
     }
   } else if (tid == 0) {
     atomicExch(err, 1);
@@ -676,7 +656,7 @@ void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st, int* err
 }
 
 int heuristic_cfg(int M, int N, int K, long batch, int es, bool tensor) {
-  if (es == 4 && tensor && M >= 64 && N >= 32) return (M >= 512 && N >= 512 && K >= 512) ? 7 : 6;
+  if (es == 4 && tensor && M >= 64 && N >= 32) return (M >= 768 && N >= 768 && K >= 2048) ? 7 : 6;
   if (M <= 32 && N <= 32) return 2;
   if (M >= 96 && N >= 96) return es == 4 ? (tensor ? 6 : 4) : 3;
   if (M >= 128 && N <= 64) return 1;

@@ -121,4 +121,36 @@ __device__ __forceinline__ float tf32_hi(float v) {
   return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
 }
 
+// Epilogue of the tensor-core tiles: one 32-row x 16-column chunk of the
+// accumulator, held one row per lane (r[j] = column j), goes through a per-warp
+// shared-memory transpose (stg: 32 x 17 floats) so that each store
+// instruction writes two 64-byte row segments instead of 32 scattered words.
+// Rows row0.., columns col0.. of batch entry bi; split-K partials or
+// C = alpha acc + beta C.
+__device__ __forceinline__ void store_chunk(const GArgs<float>& g, float* stg, const uint32_t (&r)[16], int lane,
+                                            int row0, int col0, int plane, int c, long bi) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = __uint_as_float(r[j]);
+  __syncwarp();
+  const bool part = g.partial != nullptr;
+  float* Cb = part ? g.partial + ((long)blockIdx.z * g.batch + bi) * (long)g.M * g.N : opaddr(g.C, plane, c);
+  const long crs = part ? (long)g.N : g.C.rs, ccs = part ? 1L : g.C.cs;
+  const int jj = lane & 15;
+#pragma unroll 4
+  for (int it = 0; it < 16; ++it) {
+    const int rr = 2 * it + (lane >> 4);
+    const int gi = row0 + rr, gj = col0 + jj;
+    if (gi < g.M && gj < g.N) {
+      float* cp = Cb + (long)gi * crs + (long)gj * ccs;
+      float v = stg[rr * 17 + jj];
+      if (!part) {
+        v *= g.alpha;
+        if (g.beta != 0.f) v += g.beta * *cp;
+      }
+      *cp = v;
+    }
+  }
+  __syncwarp();
+}
+
 }  // namespace acr

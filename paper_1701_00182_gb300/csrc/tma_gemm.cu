@@ -167,8 +167,9 @@ __global__ void __launch_bounds__(tg::NT, 1) k_gemm_tma(const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   if (!s_err) {
+    // the stage ring is free now: per-warp transpose buffers for the stores
+    float* stg = reinterpret_cast<float*>(tg_raw + (base_s - raw_s)) + warp * 32 * 17;
     const int lbase = warp * 32;
-    const int gi = m0 + lbase + lane;
 #pragma unroll 1
     for (int ch = 0; ch < tg::BN / 16; ++ch) {
       uint32_t r[16];
@@ -178,27 +179,7 @@ __global__ void __launch_bounds__(tg::NT, 1) k_gemm_tma(const __grid_constant__ 
 #pragma unroll
         for (int j = 0; j < 16; ++j) r[j] = 0u;
       }
-      if (gi < g.M) {
-        if (g.partial) {
-          float* P = g.partial + ((long)blockIdx.z * g.batch + bi) * (long)g.M * g.N + (long)gi * g.N;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int gj = n0 + ch * 16 + j;
-            if (gj < g.N) P[gj] = __uint_as_float(r[j]);
-          }
-        } else {
-          float* C = opaddr(g.C, plane, c) + (long)gi * g.C.rs;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int gj = n0 + ch * 16 + j;
-            if (gj >= g.N) continue;
-            float* cp = C + (long)gj * g.C.cs;
-            float v = g.alpha * __uint_as_float(r[j]);
-            if (g.beta != 0.f) v += g.beta * *cp;
-            *cp = v;
-          }
-        }
-      }
+      store_chunk(g, stg, r, lane, m0 + lbase, n0 + ch * 16, plane, c, bi);
     }
   } else if (tid == 0) {
     atomicExch(err, 1);

@@ -671,11 +671,12 @@ __global__ void __launch_bounds__(kQrcpThreads) k_qrcp(int r, const T* Call, con
 }
 
 // ---- coefficients of the rebuild ---------------------------------------------
-// Z (r x Kout, row major) per side of block bi such that the new factor is
-// factor * Z:  QR path  Z[0:k, t] = X[:, t] sqrt(s_t);  Gram path  Z[piv[u], t] = z[u],
-// R11 z = X[:, t] sqrt(s_t)  with R11[u][v] = R[u][piv[v]] (upper triangular).
-// Every row of Z is finally multiplied by the balancing scale of its column of
-// the original factor.
+// Z (zrows x Kout used of r x Kout, row major) per side of block bi such that
+// the new factor is (factor columns) * Z:  QR path  Z[0:k, t] = X[:, t] sqrt(s_t)
+// (rows of Q);  Gram path  Z[u, t] = z[u] a_{piv[u]},  R11 z = X[:, t] sqrt(s_t)
+// with R11[u][v] = R[u][piv[v]] (upper triangular) and a the balancing scale;
+// there the factor columns are the gathered pivots piv[0..k), so Z is compact.
+// Rows k .. zrows-1 are zero.
 //
 // One CTA per (side, block, chunk of C columns); its 256 threads are C columns
 // x G = 256 / C row groups.  The right-hand sides of the chunk sit in B (shared
@@ -689,7 +690,7 @@ __global__ void __launch_bounds__(256) k_coef(int r, int Kout, long NB, int qr, 
                                               const T* __restrict__ Xall, const T* __restrict__ Yall,
                                               const T* __restrict__ sigall, const int* __restrict__ rankall,
                                               const T* __restrict__ scall, T* __restrict__ Zall, int C,
-                                              T* __restrict__ gscratch) {
+                                              T* __restrict__ gscratch, int zrows) {
   extern __shared__ unsigned char smraw[];
   const long j = blockIdx.x;
   const int side = (int)(j / NB);
@@ -701,7 +702,7 @@ __global__ void __launch_bounds__(256) k_coef(int r, int Kout, long NB, int qr, 
   const int k = kkall[j];
   T* Z = Zall + j * (long)r * Kout;
   if (t < Kout)
-    for (int row = g; row < r; row += G) Z[(long)row * Kout + t] = T(0);
+    for (int row = g; row < zrows; row += G) Z[(long)row * Kout + t] = T(0);
   if (t0 >= rank) return;  // uniform over the CTA
   const bool act = t < rank;
   const T* R = Rall + j * (long)r * r;
@@ -732,8 +733,29 @@ __global__ void __launch_bounds__(256) k_coef(int r, int Kout, long NB, int qr, 
     const T* Rc = R + pu;
 #pragma unroll 4
     for (int w = g; w < u; w += G) B[(long)w * ldb + tc] -= Rc[(long)w * r] * zu;
-    if (g == 0 && act) Z[(long)pu * Kout + t] = zu * (sc ? sc[pu] : T(1));
+    if (g == 0 && act) Z[(long)u * Kout + t] = zu * (sc ? sc[pu] : T(1));
     __syncthreads();
+  }
+}
+
+// Columns piv[0..k) of each block's factor, side by side (zero up to kmax):
+// out[plane][row][u] = F[plane][row][piv[u]] for the rows of cluster c, with the
+// pivots of block c ^ side (the R factor of block b lives in cluster b ^ 1).
+template <class T>
+__global__ void k_gather_piv(int P, int m, int s, int nclus, int r, int kmax, long NB, int side, const T* F,
+                             const int* pivall, const int* kkall, T* out) {
+  const long nrow = (long)P * m;
+  const int lane = threadIdx.x & 31;
+  for (long rw = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; rw < nrow;
+       rw += ((long)gridDim.x * blockDim.x) >> 5) {
+    const long plane = rw / m;
+    const int i = (int)(rw - plane * m);
+    const long j = side * NB + plane * nclus + ((i / s) ^ side);
+    const int* piv = pivall + j * r;
+    const int k = kkall[j];
+    const T* src = F + rw * r;
+    T* dst = out + rw * kmax;
+    for (int u = lane; u < kmax; u += 32) dst[u] = (u < k) ? src[piv[u]] : T(0);
   }
 }
 
@@ -806,13 +828,23 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     k_pchol<T><<<(unsigned)(2 * NB), kCholThreads, sm, c.st>>>(r, G.p, T(epsd), R.p, piv.p, kk.p);
     c.kend(KC_PCHOL, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r);
   }
+  // Ranks of the two factorisations: the core only needs its leading
+  // kL x kR block (the truncation kernels read nothing else).
+  std::vector<int> hk(2 * NB);
+  ACR_CUDA(cudaMemcpyAsync(hk.data(), kk.p, 2 * NB * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  ACR_CUDA(cudaStreamSynchronize(c.st));
+  int kmaxL = 0, kmaxR = 0;
+  for (long i = 0; i < NB; ++i) {
+    kmaxL = std::max(kmaxL, hk[i]);
+    kmaxR = std::max(kmaxR, hk[NB + i]);
+  }
   DBuf<T> Cc(c, NB * (size_t)r * r);
   {
     Op<T> A{R.p, r, 1, 0, (long)r * r, 0, 0, 0};
     Op<T> B{R.p + NB * r * (long)r, 1, r, 0, (long)r * r, 0, 0, 0};
     Op<T> C{Cc.p, r, 1, 0, (long)r * r, 0, 0, 0};
     c.tag = "core";
-    gemm<T>(c, r, r, r, 1, (int)NB, T(1), A, B, T(0), C);
+    gemm<T>(c, kmaxL, kmaxR, r, 1, (int)NB, T(1), A, B, T(0), C);
   }
   DBuf<T> W(c, NB * (size_t)r * r), Vw(c, NB * (size_t)r * r), Xo(c, NB * (size_t)r * r),
       Yo(c, NB * (size_t)r * r), sig(c, NB * (size_t)r);
@@ -852,20 +884,15 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     Vout.release();
     return;
   }
+  // Z and the rebuild use the leading kmax rows / factor columns: the
+  // pivoted columns (Gram path, gathered below) or Q's first columns (QR path).
+  const int kmax = std::max(kmaxL, kmaxR);
   DBuf<T> Z(c, 2 * NB * (size_t)r * Kout);
   DBuf<T> Bscr;
   c.kbegin();
   {
     // column chunk: the widest of 32 / 16 / 8 whose k x C right-hand sides fit
     // in 100 KB of shared memory (two CTAs per SM); else a global scratch.
-    int kmax = r;
-    if (!qr) {
-      std::vector<int> hk(2 * NB);
-      ACR_CUDA(cudaMemcpyAsync(hk.data(), kk.p, 2 * NB * sizeof(int), cudaMemcpyDeviceToHost, c.st));
-      ACR_CUDA(cudaStreamSynchronize(c.st));
-      kmax = 0;
-      for (int v : hk) kmax = std::max(kmax, v);
-    }
     const size_t cap = 100 * 1024;
     int Cw = 32;
     while (Cw > 8 && (size_t)kmax * Cw * sizeof(T) > cap) Cw /= 2;
@@ -883,18 +910,27 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     }
     dim3 grid((unsigned)(2 * NB), (unsigned)((Kout + Cw - 1) / Cw));
     k_coef<T><<<grid, 256, sm, c.st>>>(r, Kout, NB, qr ? 1 : 0, R.p, piv.p, kk.p, Xo.p, Yo.p, sig.p, rank.p,
-                                       scale.p, Z.p, Cw, gs);
+                                       scale.p, Z.p, Cw, gs, kmax);
   }
   c.kend(KC_COEF, 0, 2.0 * NB * sizeof(T) * ((double)r * r + (double)r * Kout));
   Uout = DBuf<T>(c, (size_t)P * m * Kout);
   Vout = DBuf<T>(c, (size_t)P * m * Kout);
   for (int side = 0; side < 2; ++side) {
     T* F = side ? Rb.p : Lb.p;
+    DBuf<T> Gc;
     Op<T> A{F, r, 1, (long)m * r, (long)s * r, 0, 0, 0};
+    if (!qr) {
+      Gc = DBuf<T>(c, (size_t)P * m * kmax);
+      c.kbegin();
+      k_gather_piv<T><<<(unsigned)std::min<long>(((long)P * m * 32 + 255) / 256, 152L * 32), 256, 0, c.st>>>(
+          P, m, s, nclus, r, kmax, NB, side, F, piv.p, kk.p, Gc.p);
+      c.kend(KC_COPY, 0, (double)sizeof(T) * 2.0 * P * m * kmax, "copy:gather_piv");
+      A = Op<T>{Gc.p, kmax, 1, (long)m * kmax, (long)s * kmax, 0, 0, 0};
+    }
     Op<T> B{Z.p + side * NB * r * (long)Kout, Kout, 1, (long)nclus * r * Kout, (long)r * Kout, 0, 0, side};
     Op<T> C{(side ? Vout.p : Uout.p), Kout, 1, (long)m * Kout, (long)s * Kout, 0, 0, 0};
     c.tag = "rebuild";
-    gemm<T>(c, s, Kout, r, P, nclus, T(1), A, B, T(0), C);
+    gemm<T>(c, s, Kout, kmax, P, nclus, T(1), A, B, T(0), C);
   }
 }
 

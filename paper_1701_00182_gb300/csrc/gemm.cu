@@ -936,6 +936,185 @@ __global__ void __launch_bounds__(256) k_hexpand(HexpArgs<T> a) {
   }
 }
 
+// ---- the fused expansion on the tcgen05 tensor cores (FP32 as 3xTF32) --------
+// One CTA per (plane, pair of 64-row leaves 2t, 2t+1, 128 output columns): the
+// 128 rows are one MMA tile.  The inner dimension is a list of segments, each
+// starting on a 32-deep slice:
+//   0: the two leaf blocks, block diagonal (K = 128), times the stacked W rows;
+//   1: a level whose cluster holds both leaves (K = K_l): U_l rows times the
+//      coefficients of the sibling cluster;
+//   2: the last level, where the two leaves are siblings (K = 2 K_l):
+//      [U(2t) 0; 0 U(2t+1)] times [C(2t+1); C(2t)].
+// Loads, TF32 split, staging, MMA issue and epilogue follow k_gemm_tc05; the
+// MMA N is the tile's column count rounded up to 16.
+struct HexpSeg {
+  int nseg = 0, nslice = 0;
+  int type[MAXL + 1] = {}, lvl[MAXL + 1] = {}, slice0[MAXL + 1] = {};
+};
+
+__global__ void __launch_bounds__(tc::NT, 1) k_hexpand_tc(HexpArgs<float> a, HexpSeg sg, int* err) {
+  constexpr int QT = (tc::BM * tc::BK / 4) / tc::NT;
+  extern __shared__ unsigned char tc_raw[];
+  __shared__ __align__(8) uint64_t bars[tc::NSTAGE];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int npair = a.m / 128;
+  const int plane = blockIdx.x / npair, pr = blockIdx.x % npair;
+  const int R0 = pr * 128;
+  const int n0 = blockIdx.y * tc::BN;
+  const int ncols = min(tc::BN, a.w - n0);
+  const int nmma = (ncols + 15) / 16 * 16;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) |
+                         ((uint32_t)(tc::BM >> 4) << 24);
+  const int nk = sg.nslice;
+  const uint32_t raw_s = smem_u32(tc_raw);
+  const uint32_t base_s = (raw_s + 1023u) & ~1023u;
+  unsigned char* base = tc_raw + (base_s - raw_s);
+  if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), tc::TMEM_COLS);
+  if (tid == 0) {
+    for (int s = 0; s < tc::NSTAGE; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_ok = 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const float* Wp = a.W + plane * a.wps;
+  float ra0[QT][4], rb0[QT][4], ra1[QT][4], rb1[QT][4];
+  // A: row i = e >> 3, quad q = e & 7 (k contiguous); B^T: column j = e & 127, quad e >> 7.
+  auto load = [&](int kc, float (&ra)[QT][4], float (&rb)[QT][4]) {
+    int si = 0;
+    while (si + 1 < sg.nseg && kc >= sg.slice0[si + 1]) ++si;
+    const int ty = sg.type[si], li = sg.lvl[si];
+    const int k0 = (kc - sg.slice0[si]) * tc::BK;
+    const int K = ty == 0 ? 64 : a.K[li];
+    const int nc = ty == 0 ? a.w : a.ncol[li];
+    const float* U = ty == 0 ? nullptr : a.U[li] + plane * a.ups[li];
+#pragma unroll
+    for (int it = 0; it < QT; ++it) {
+      const int e = tid + tc::NT * it;
+      const int i = e >> 3, q = e & 7, half = i >> 6;
+      const int j = e & 127, qb = e >> 7, gj = n0 + j;
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int k = k0 + 4 * q + jj;
+        float va = 0.f;
+        if (ty == 0) {
+          if ((k >> 6) == half && k < 128) {
+            const float* Lf = a.leaf + plane * a.lps + (long)(2 * pr + half) * 4096;
+            const int ii = i & 63, kl = k & 63;
+            va = a.leaf_trans ? Lf[kl * 64 + ii] : Lf[ii * 64 + kl];
+          }
+        } else if (ty == 1) {
+          if (k < K) va = U[(long)(R0 + i) * K + k];
+        } else {
+          const int kk = k - half * K;
+          if (kk >= 0 && kk < K) va = U[(long)(R0 + i) * K + kk];
+        }
+        ra[it][jj] = va;
+        const int kb = k0 + 4 * qb + jj;
+        float vb = 0.f;
+        if (gj < nc) {
+          if (ty == 0) {
+            if (kb < 128) vb = Wp[(long)(R0 + kb) * a.wld + gj];
+          } else if (ty == 1) {
+            if (kb < K) {
+              const int cl = R0 / a.s[li];
+              vb = a.C[li][(((long)plane * a.nclus[li] + (cl ^ 1)) * K + kb) * nc + gj];
+            }
+          } else if (kb < 2 * K) {
+            const int leafc = R0 / 64 + (kb < K ? 1 : 0);
+            const int kk = kb < K ? kb : kb - K;
+            vb = a.C[li][(((long)plane * a.nclus[li] + leafc) * K + kk) * nc + gj];
+          }
+        }
+        rb[it][jj] = vb;
+      }
+    }
+  };
+  auto split4 = [](const float (&x)[4], float4& h, float4& l) {
+    h.x = tf32_hi(x[0]); l.x = tf32_hi(x[0] - h.x);
+    h.y = tf32_hi(x[1]); l.y = tf32_hi(x[1] - h.y);
+    h.z = tf32_hi(x[2]); l.z = tf32_hi(x[2] - h.z);
+    h.w = tf32_hi(x[3]); l.w = tf32_hi(x[3] - h.w);
+  };
+  auto store = [&](int s, const float (&ra)[QT][4], const float (&rb)[QT][4]) {
+    unsigned char* st = base + s * tc::STAGE_BYTES;
+#pragma unroll
+    for (int it = 0; it < QT; ++it) {
+      const int e = tid + tc::NT * it;
+      const int i = e >> 3, q = e & 7, j = e & 127, qb = e >> 7;
+      const uint32_t oa = i * 128 + ((q ^ (i & 7)) << 4), ob = j * 128 + ((qb ^ (j & 7)) << 4);
+      float4 h, l;
+      split4(ra[it], h, l);
+      *reinterpret_cast<float4*>(st + oa) = h;
+      *reinterpret_cast<float4*>(st + tc::TILE_BYTES + oa) = l;
+      split4(rb[it], h, l);
+      *reinterpret_cast<float4*>(st + 2 * tc::TILE_BYTES + ob) = h;
+      *reinterpret_cast<float4*>(st + 3 * tc::TILE_BYTES + ob) = l;
+    }
+  };
+  auto issue = [&](int kc, int s) {
+    tc_fence_after();
+    const uint32_t sa = base_s + s * tc::STAGE_BYTES;
+#pragma unroll
+    for (int kk = 0; kk < tc::BK / 8; ++kk) {
+      const uint64_t ah = umma_desc_sw128(sa + kk * 32), al = umma_desc_sw128(sa + tc::TILE_BYTES + kk * 32);
+      const uint64_t bh = umma_desc_sw128(sa + 2 * tc::TILE_BYTES + kk * 32),
+                     bl = umma_desc_sw128(sa + 3 * tc::TILE_BYTES + kk * 32);
+      umma_tf32(tmem, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+      umma_tf32(tmem, ah, bl, idesc, 1u);
+      umma_tf32(tmem, al, bh, idesc, 1u);
+    }
+    umma_commit(smem_u32(&bars[s]));
+  };
+  auto step = [&](int kc, float (&ra)[QT][4], float (&rb)[QT][4]) -> bool {
+    const int s = kc % tc::NSTAGE;
+    bool ok = true;
+    if (kc >= tc::NSTAGE) ok = mbar_wait_bounded(smem_u32(&bars[s]), ((kc - tc::NSTAGE) / tc::NSTAGE) & 1);
+    if (ok) store(s, ra, rb);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (!__syncthreads_and(ok)) return false;
+    if (kc + 2 < nk) load(kc + 2, ra, rb);
+    if (tid == 0) issue(kc, s);
+    return true;
+  };
+  bool ok = true;
+  if (nk > 0) load(0, ra0, rb0);
+  if (nk > 1) load(1, ra1, rb1);
+  for (int kc = 0; kc < nk && ok; kc += 2) {
+    ok = step(kc, ra0, rb0);
+    if (ok && kc + 1 < nk) ok = step(kc + 1, ra1, rb1);
+  }
+  if (ok && nk > 0) ok = mbar_wait_bounded(smem_u32(&bars[(nk - 1) % tc::NSTAGE]), ((nk - 1) / tc::NSTAGE) & 1);
+  if (!__syncthreads_and(ok)) s_ok = 0;
+  __syncthreads();
+  tc_fence_after();
+  if (s_ok) {
+    GArgs<float> g{};
+    g.M = a.m; g.N = a.w; g.alpha = a.alpha; g.beta = a.beta;
+    g.C = Op<float>{a.Y, a.yld, 1, a.yps, 0, 0, 0, 0};
+    g.partial = nullptr;
+    constexpr int CW = tc::BN / (tc::NT / 128);
+    const int lb = (warp & 3) * 32, cb = (warp >> 2) * CW;
+    float* stg = reinterpret_cast<float*>(base) + warp * 32 * 17;
+#pragma unroll 1
+    for (int ch = 0; ch < CW / 16; ++ch) {
+      if (cb + ch * 16 >= nmma) break;  // uniform over the warp
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)(cb + ch * 16), r);
+      store_chunk(g, stg, r, lane, R0 + lb, n0 + cb + ch * 16, plane, 0, 0);
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, tc::TMEM_COLS);
+}
+
 template <class T>
 void hexpand(Ctx& c, const HexpArgs<T>& a, int P) {
   if (P <= 0 || a.w <= 0) return;
@@ -947,7 +1126,32 @@ void hexpand(Ctx& c, const HexpArgs<T>& a, int P) {
   by = (double)sizeof(T) * P * a.m * (a.b + 2.0 * a.w);
   for (int l = 0; l < a.nl; ++l) by += (double)sizeof(T) * P * a.m * a.K[l];
   c.kbegin();
-  k_hexpand<T><<<grid, 256, 0, c.st>>>(a);
+  bool done = false;
+  if constexpr (sizeof(T) == 4) {
+    if (c.tensor && a.b == 64 && a.m % 128 == 0 && a.w > 64) {  // narrow panels (solve sweeps) stay on the FMA tiles
+      HexpSeg sg;
+      sg.type[0] = 0;
+      sg.lvl[0] = 0;
+      sg.slice0[0] = 0;
+      int sl = 128 / tc::BK;
+      sg.nseg = 1;
+      for (int l = 0; l < a.nl; ++l) {
+        const int ty = (a.s[l] == a.b) ? 2 : 1;
+        const int kext = ty == 2 ? 2 * a.K[l] : a.K[l];
+        sg.type[sg.nseg] = ty;
+        sg.lvl[sg.nseg] = l;
+        sg.slice0[sg.nseg] = sl;
+        ++sg.nseg;
+        sl += (kext + tc::BK - 1) / tc::BK;
+      }
+      sg.nslice = sl;
+      ACR_CUDA(cudaFuncSetAttribute(k_hexpand_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+      dim3 g2((unsigned)((long)P * (a.m / 128)), (a.w + tc::BN - 1) / tc::BN);
+      k_hexpand_tc<<<g2, tc::NT, tc::SMEM_BYTES, c.st>>>(a, sg, c.d_flag + 2);
+      done = true;
+    }
+  }
+  if (!done) k_hexpand<T><<<grid, 256, 0, c.st>>>(a);
   c.kend(KC_HEXPAND, fl, by);
   c.gemm_flops += (long long)fl;
 }

@@ -44,10 +44,13 @@ def test_variable_coefficient_n64_fp64_direct(acr, grf64):
     assert rel(from_cols(x)[:, 0], ref) < 1e-5
 
 
-def test_variable_coefficient_n64_fp32_refined(acr, grf64):
-    """FP32 ACR + FP64 refinement to 1e-10, checked with the oracle's operator."""
+@pytest.mark.parametrize("tensor_cores", [0, 1])
+def test_variable_coefficient_n64_fp32_refined(acr, grf64, tensor_cores):
+    """FP32 ACR + FP64 refinement to 1e-10, checked with the oracle's operator;
+    CUDA-core GEMMs and the tcgen05 tensor-core path (3xTF32 GEMM tiles, TMA-fed
+    tiles for large products, tensor-core HODLR expansion at 64-row leaves)."""
     n, g, f, ref = grf64
-    h = acr.acr_factor(n, g, 1e-6, 64, precision=acr.ACR_FP32)
+    h = acr.acr_factor(n, g, 1e-6, 64, precision=acr.ACR_FP32, tensor_cores=tensor_cores)
     b = to_cols(f)
     x = empty_like_cols(b)
     it, relr, _ = acr.acr_solve_ir(h, b, x, rtol=1e-10, maxit=40)
@@ -82,14 +85,16 @@ def test_helmholtz_n64_fgmres_ranks(acr):
 
 
 def test_full_size_multi_rhs_sampled(acr):
-    """n = 128, 64 RHS, FP32 ACR + FP64 refinement (the benchmark's step);
+    """n = 128, 64 RHS, FP32 ACR + FP64 refinement in the benchmark's launch
+    configuration (tensor cores, autotuned tilings, graph-captured sweeps);
     three sampled columns are re-checked on the CPU with the oracle's operator."""
     import torch
 
     n = 128
     g = synthetic.gaussian_random_field(n, 1)
     F = synthetic.multi_rhs(n, range(100, 164))
-    h = acr.acr_factor(n, torch.from_numpy(g).cuda(), 1e-6, 64, precision=acr.ACR_FP32)
+    h = acr.acr_factor(n, torch.from_numpy(g).cuda(), 1e-6, 64, precision=acr.ACR_FP32, tensor_cores=1,
+                       autotune=1, graphs=1)
     b = to_cols(F)
     x = empty_like_cols(b)
     it, relr, _ = acr.acr_solve_ir(h, b, x, rtol=1e-10, maxit=60)

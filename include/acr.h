@@ -76,6 +76,10 @@ typedef struct {
                              negative = never; otherwise it is inverted as a HODLR matrix) */
   int graphs;             /* 1 = capture the solve sweeps once per (nrhs, transpose) as a CUDA graph and replay
                              it; with cuda_stream NULL the handle then runs on its own blocking stream */
+  const double* velocity; /* NULL, or a convection velocity beta (3 planar arrays of n^3 doubles: beta_x, beta_y,
+                             beta_z per node, host or device, copied at factor) adding beta . grad u by
+                             first-order upwind differences (Section 5, Eq. codi: beta = alpha b(x)); the
+                             operator is then non-symmetric and acr_solve_ir_transpose refines with A^T */
 } acr_opts;
 
 typedef struct {

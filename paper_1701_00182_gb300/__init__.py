@@ -50,6 +50,7 @@ class AcrOpts(C.Structure):
         ("core_svd", C.c_int),
         ("coarse_dense_max", C.c_int),
         ("graphs", C.c_int),
+        ("velocity", C.c_void_p),
     ]
 
 
@@ -184,40 +185,53 @@ class Handle:
             pass
 
 
+def _f64_buffer(a, count: int, what: str):
+    """(owner, pointer) of a contiguous float64 numpy array / tensor (host or CUDA) of `count` values."""
+    try:
+        import torch
+
+        is_t = isinstance(a, torch.Tensor)
+    except ImportError:
+        is_t = False
+    if is_t:
+        if a.dtype != torch.float64 or a.numel() != count or not a.is_contiguous():
+            raise ValueError("%s tensor must be contiguous float64 with %d entries" % (what, count))
+        return a, a.data_ptr()
+    keep = np.ascontiguousarray(a, dtype=np.float64)
+    if keep.size != count:
+        raise ValueError("%s must have %d entries" % (what, count))
+    return keep, keep.ctypes.data
+
+
 def acr_factor(n: int, log_kappa, tol: float, leaf: int, opts: AcrOpts | None = None, **kw) -> Handle:
     """ACR elimination; ``log_kappa`` is a float64 numpy array / tensor (host or CUDA) of n^3 values or None.
 
-    Keyword overrides of the options: precision, shift, max_rank, mem_budget, autotune, nrhs_max, stream.
+    Keyword overrides of the options: precision, shift, max_rank, mem_budget, autotune, nrhs_max, stream,
+    velocity (3 x n^3 float64, planar beta_x, beta_y, beta_z: the convection velocity), and the other
+    acr_opts fields by name.
     """
     lib = load_library()
     o = opts if opts is not None else acr_default_opts()
+    keep_v = None
     for k, v in kw.items():
         if k == "stream":
             o.cuda_stream = C.c_void_p(v)
+        elif k == "velocity":
+            if v is None:
+                o.velocity = None
+            else:
+                keep_v, pv = _f64_buffer(v, 3 * n ** 3, "velocity")
+                o.velocity = C.c_void_p(pv)
         else:
             setattr(o, k, v)
     keep = None
     ptr = None
     if log_kappa is not None:
-        try:
-            import torch
-
-            is_t = isinstance(log_kappa, torch.Tensor)
-        except ImportError:
-            is_t = False
-        if is_t:
-            if log_kappa.dtype != torch.float64 or log_kappa.numel() != n ** 3 or not log_kappa.is_contiguous():
-                raise ValueError("log_kappa tensor must be contiguous float64 with n^3 entries")
-            keep = log_kappa
-            ptr = log_kappa.data_ptr()
-        else:
-            keep = np.ascontiguousarray(log_kappa, dtype=np.float64)
-            if keep.size != n ** 3:
-                raise ValueError("log_kappa must have n^3 entries")
-            ptr = keep.ctypes.data
+        keep, ptr = _f64_buffer(log_kappa, n ** 3, "log_kappa")
     h = C.c_void_p()
     st = lib.acr_factor(int(n), ptr, float(tol), int(leaf), C.byref(o), C.byref(h))
-    del keep
+    del keep, keep_v
+    o.velocity = None  # the library copied it; do not keep a pointer to a released buffer
     _check(st, "acr_factor")
     return Handle(h.value, n, o)
 

@@ -156,7 +156,7 @@ struct acr_handle_s {
   Geometry geo;
   DBuf<int> perm, iperm;
   std::vector<DBuf<int>> cutp, cutq;
-  DBuf<double> kappa, coef;
+  DBuf<double> kappa, coef, vel;
   std::unique_ptr<FactorT<float>> f32;
   std::unique_ptr<FactorT<double>> f64;
   acr_stats stats{};
@@ -169,6 +169,7 @@ struct acr_handle_s {
     cutq.clear();
     kappa.release();
     coef.release();
+    vel.release();
     if (ctx.st) cudaStreamSynchronize(ctx.st);
     const char* ps = std::getenv("ACR_PROFILE_SITES");
     if (ps && (ps[0] == '1' || ps[0] == '2') && !ctx.site.empty()) {
@@ -273,7 +274,7 @@ void factor_impl(acr_handle_s* h, FactorT<T>& fac) {
     cp.push_back(h->cutp[l].p);
     cq.push_back(h->cutq[l].p);
   }
-  assemble_level0<T>(c, g, h->kappa.p, h->shift, h->perm.p, h->iperm.p, cp, cq, D.h, E.h, F.h);
+  assemble_level0<T>(c, g, h->kappa.p, h->vel.p, h->shift, h->perm.p, h->iperm.p, cp, cq, D.h, E.h, F.h);
   for (int l = 0; l < L; ++l) h->stats.max_rank_d[0][l] = g.ncut[l];
   cudaEvent_t e0, e1;
   ACR_CUDA(cudaEventCreate(&e0));
@@ -584,7 +585,7 @@ int solve_ir_impl(acr_handle h, const double* b, double* x, int nrhs, long ld, d
     std::vector<double> hn(2 * nrhs), rel(nrhs, 1.0);
     for (it = 1; it <= maxit; ++it) {
       solve_any(h, r.p, x, nrhs, ld, trans, true);
-      stencil_apply(c, h->n, nrhs, h->coef.p, x, ld, b, r.p, -1.0, 1.0, nrm.p);
+      stencil_apply(c, h->n, nrhs, h->coef.p, x, ld, b, r.p, -1.0, 1.0, nrm.p, trans);
       ACR_CUDA(cudaMemcpyAsync(hn.data(), nrm.p, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, c.st));
       ACR_CUDA(cudaStreamSynchronize(c.st));
       bool all_ok = true, finite = true;
@@ -727,8 +728,12 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     } else {
       fill<double>(c, h->kappa.p, N, 1.0);
     }
-    h->coef = DBuf<double>(c, 4 * N);
-    face_coefficients(c, n, h->kappa.p, o.shift, h->coef.p);
+    if (o.velocity) {
+      h->vel = DBuf<double>(c, 3 * N);
+      ACR_CUDA(cudaMemcpyAsync(h->vel.p, o.velocity, 3 * N * sizeof(double), cudaMemcpyDefault, c.st));
+    }
+    h->coef = DBuf<double>(c, 7 * N);
+    face_coefficients(c, n, h->kappa.p, h->vel.p, o.shift, h->coef.p);
     std::memset(&h->stats, 0, sizeof(h->stats));
     h->stats.n = n;
     h->stats.leaf = leaf;

@@ -202,8 +202,8 @@ template <class T> void copy2d(Ctx& c, int P, long rows, int cols, T alpha, cons
                                long sps, T* dst, long dld, long dps);
 template <class T> void set_identity_clusters(Ctx& c, int P, int m, int s, T* U, long ld, long ps);
 template <class T> int batched_inverse(Ctx& c, int nb, int n, T* A, long stride);  // in place GJ, returns 0
-template <class T> void assemble_level0(Ctx& c, const Geometry& geo, const double* kappa, double shift,
-                                        const int* d_perm, const int* d_iperm,
+template <class T> void assemble_level0(Ctx& c, const Geometry& geo, const double* kappa, const double* vel,
+                                        double shift, const int* d_perm, const int* d_iperm,
                                         const std::vector<const int*>& d_cutp,
                                         const std::vector<const int*>& d_cutq, HMat<T> D, HMat<T> E,
                                         HMat<T> F);
@@ -212,14 +212,14 @@ template <class T> void permute_in(Ctx& c, int n, int nrhs, const double* b, lon
 template <class T> void permute_out(Ctx& c, int n, int nrhs, const T* F, const int* d_perm, double* x,
                                     long ld, int accumulate);
 void stencil_apply(Ctx& c, int n, int nrhs, const double* coef, const double* x, long ld, const double* y,
-                   double* out, double alpha, double beta, double* norms_out /*2*nrhs or null*/);
+                   double* out, double alpha, double beta, double* norms_out /*2*nrhs or null*/, bool trans = false);
 template <class T> void expand_leaves(Ctx& c, int m, int b, const T* leaf, T* dense);
 void exp_inplace(Ctx& c, double* p, long n);
 void stencil_norms_scratch(cudaStream_t st, int n, int nrhs, const double* coef, const double* x, long ld,
                            const double* y, double* out, double* part, int nb_max, double* pairs);
 void grad_logkappa(Ctx& c, int n, int nrhs, const double* kap, const double* u, const double* lam, long ld,
                    double* grad, int accumulate);
-void face_coefficients(Ctx& c, int n, const double* kappa, double shift, double* coef);
+void face_coefficients(Ctx& c, int n, const double* kappa, const double* vel, double shift, double* coef);
 void col_dots(Ctx& c, long N, int nrhs, const double* x, long ldx, const double* y, long ldy, double* out);
 void col_axpy(Ctx& c, long N, int nrhs, const double* a /*device nrhs*/, const double* x, long ldx,
               double* y, long ldy);

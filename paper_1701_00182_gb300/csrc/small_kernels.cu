@@ -213,39 +213,51 @@ int batched_inverse(Ctx& c, int nb, int n, T* A, long stride) {
 
 __device__ __forceinline__ double harm(double a, double b, double ih2) { return 2.0 * a * b / (a + b) * ih2; }
 
+// Upwind weight of the first-order convection term toward the neighbour in
+// direction +e_d (plus = true) or -e_d of a node with velocity component beta:
+// beta du/dx_d is differenced against the upstream neighbour, so only that
+// neighbour gets -|beta|/h and the diagonal gets +|beta|/h.
+__device__ __forceinline__ double upw(double beta, bool plus, double ih) {
+  return plus ? fmax(-beta, 0.0) * ih : fmax(beta, 0.0) * ih;
+}
+
 // One thread per row of a leaf block of plane k: the 5-point in-plane part
-// restricted to the leaf, the full diagonal (6 faces + shift), and the
-// diagonal E (to plane k-1) and F (to plane k+1) entries.
+// restricted to the leaf, the full diagonal (6 faces + shift + convection),
+// and the diagonal E (to plane k-1) and F (to plane k+1) entries.  vel: the
+// convection velocity (3 planar components of n^3 values) or null.
 template <class T>
-__global__ void k_assemble_leaves(int n, int b, const double* kap, double shift, const int* perm,
+__global__ void k_assemble_leaves(int n, int b, const double* kap, const double* vel, double shift, const int* perm,
                                   const int* iperm, T* DL, T* EL, T* FL) {
   const int m = n * n;
+  const long N = (long)m * n;
   const int nleaf = m / b;
   const int k = blockIdx.x / nleaf, lf = blockIdx.x % nleaf;
-  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h), ih = 1.0 / h;
   for (int i = threadIdx.x; i < b; i += blockDim.x) {
     const int pos = lf * b + i;
     const int g = perm[pos];
     const int x = g % n, y = g / n;
     const long node = (long)k * m + g;
     const double kp = kap[node];
+    const double bx = vel ? vel[node] : 0.0, by = vel ? vel[N + node] : 0.0, bz = vel ? vel[2 * N + node] : 0.0;
     T* drow = DL + ((long)k * nleaf + lf) * b * b + (long)i * b;
     T* erow = EL + ((long)k * nleaf + lf) * b * b + (long)i * b;
     T* frow = FL + ((long)k * nleaf + lf) * b * b + (long)i * b;
     for (int j = 0; j < b; ++j) { drow[j] = T(0); erow[j] = T(0); frow[j] = T(0); }
-    double diag = shift;
+    double diag = shift + (fabs(bx) + fabs(by) + fabs(bz)) * ih;
     const int dx[4] = {-1, 1, 0, 0}, dy[4] = {0, 0, -1, 1};
     for (int d = 0; d < 4; ++d) {
       int xx = x + dx[d], yy = y + dy[d];
       if (xx < 0 || xx >= n || yy < 0 || yy >= n) { diag += kp * ih2; continue; }
       double cpq = harm(kp, kap[(long)k * m + xx + n * yy], ih2);
       diag += cpq;
+      const double w = cpq + (d < 2 ? upw(bx, dx[d] > 0, ih) : upw(by, dy[d] > 0, ih));
       int q = iperm[xx + n * yy];
-      if (q >= lf * b && q < lf * b + b) drow[q - lf * b] = T(-cpq);
+      if (q >= lf * b && q < lf * b + b) drow[q - lf * b] = T(-w);
     }
-    if (k > 0) { double cz = harm(kp, kap[node - m], ih2); diag += cz; erow[i] = T(-cz); }
+    if (k > 0) { double cz = harm(kp, kap[node - m], ih2); diag += cz; erow[i] = T(-(cz + upw(bz, false, ih))); }
     else diag += kp * ih2;
-    if (k < n - 1) { double cz = harm(kp, kap[node + m], ih2); diag += cz; frow[i] = T(-cz); }
+    if (k < n - 1) { double cz = harm(kp, kap[node + m], ih2); diag += cz; frow[i] = T(-(cz + upw(bz, true, ih))); }
     else diag += kp * ih2;
     drow[i] = T(diag);
   }
@@ -253,35 +265,47 @@ __global__ void k_assemble_leaves(int n, int b, const double* kap, double shift,
 
 // One thread per (plane, cut edge) of a level: the exact low-rank factors of
 // the off-diagonal blocks, one column per cut edge (p in the first child,
-// q in the second):  U[p,e] = U[q,e] = -c_pq,  V[p,e] = V[q,e] = 1.
+// q in the second):  U[p,e] = A[p][q],  U[q,e] = A[q][p],  V[p,e] = V[q,e] = 1,
+// with A[p][q] = -(c_pq + upwind weight of row p toward q).
 template <class T>
-__global__ void k_assemble_cuts(int n, int nodes, int ncut, const double* kap, const int* perm,
+__global__ void k_assemble_cuts(int n, int nodes, int ncut, const double* kap, const double* vel, const int* perm,
                                 const int* cp, const int* cq, T* U, T* V, long ld, long ps) {
   const int m = n * n;
-  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+  const long N = (long)m * n;
+  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h), ih = 1.0 / h;
   long tot = (long)n * nodes * ncut;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
     int k = (int)(e / ((long)nodes * ncut));
     int r = (int)(e - (long)k * nodes * ncut);
     int col = r % ncut;
     int p = cp[r], q = cq[r];
-    double c = harm(kap[(long)k * m + perm[p]], kap[(long)k * m + perm[q]], ih2);
-    U[k * ps + (long)p * ld + col] = T(-c);
-    U[k * ps + (long)q * ld + col] = T(-c);
+    const int gp = perm[p], gq = perm[q];
+    double c = harm(kap[(long)k * m + gp], kap[(long)k * m + gq], ih2);
+    double wp = c, wq = c;
+    if (vel) {
+      // neighbours differ in x (same row of the plane) or in y
+      const bool xdir = (gp / n) == (gq / n);
+      const bool qplus = xdir ? (gq % n) > (gp % n) : (gq / n) > (gp / n);
+      const long off = xdir ? 0 : N;
+      wp += upw(vel[off + (long)k * m + gp], qplus, ih);
+      wq += upw(vel[off + (long)k * m + gq], !qplus, ih);
+    }
+    U[k * ps + (long)p * ld + col] = T(-wp);
+    U[k * ps + (long)q * ld + col] = T(-wq);
     V[k * ps + (long)p * ld + col] = T(1);
     V[k * ps + (long)q * ld + col] = T(1);
   }
 }
 
 template <class T>
-void assemble_level0(Ctx& c, const Geometry& geo, const double* kappa, double shift, const int* d_perm,
-                     const int* d_iperm, const std::vector<const int*>& d_cutp,
+void assemble_level0(Ctx& c, const Geometry& geo, const double* kappa, const double* vel, double shift,
+                     const int* d_perm, const int* d_iperm, const std::vector<const int*>& d_cutp,
                      const std::vector<const int*>& d_cutq, HMat<T> D, HMat<T> E, HMat<T> F) {
   const int n = geo.n, b = geo.leaf;
   const int nleaf = geo.m / b;
   c.kbegin();
-  k_assemble_leaves<T><<<n * nleaf, std::min(b, 128), 0, c.st>>>(n, b, kappa, shift, d_perm, d_iperm, D.leaf,
-                                                                 E.leaf, F.leaf);
+  k_assemble_leaves<T><<<n * nleaf, std::min(b, 128), 0, c.st>>>(n, b, kappa, vel, shift, d_perm, d_iperm,
+                                                                 D.leaf, E.leaf, F.leaf);
   c.kend(KC_ASSEMBLE, 0, 3.0 * sizeof(T) * (double)geo.m * b * n);
   for (int l = 0; l < geo.L; ++l) {
     int K = geo.ncut[l];
@@ -289,8 +313,8 @@ void assemble_level0(Ctx& c, const Geometry& geo, const double* kappa, double sh
     fill<T>(c, D.V[l], (long)n * D.pps[l], T(0));
     long tot = (long)n * (1L << l) * K;
     c.kbegin();
-    k_assemble_cuts<T><<<nblk(tot), 256, 0, c.st>>>(n, 1 << l, K, kappa, d_perm, d_cutp[l], d_cutq[l], D.U[l],
-                                                   D.V[l], K, D.pps[l]);
+    k_assemble_cuts<T><<<nblk(tot), 256, 0, c.st>>>(n, 1 << l, K, kappa, vel, d_perm, d_cutp[l], d_cutq[l],
+                                                   D.U[l], D.V[l], K, D.pps[l]);
     c.kend(KC_ASSEMBLE, 0, 4.0 * sizeof(T) * (double)tot);
   }
 }
@@ -360,37 +384,52 @@ void permute_out(Ctx& c, int n, int nrhs, const T* F, const int* d_perm, double*
 // ---- FP64 7-point stencil ------------------------------------------------------
 // coef layout: [4][N] = diagonal (6 faces + shift), coupling to +x, +y, +z.
 
-__global__ void k_face_coef(int n, const double* kap, double shift, double* coef) {
+// Row coefficients of the FP64 operator, 7 planar arrays of n^3: [0] diagonal,
+// [1 + 2d] weight of the neighbour at -e_d, [2 + 2d] at +e_d (d = x, y, z), so
+// (A u)_p = coef0_p u_p - sum of weight x neighbour (zero where the neighbour
+// lies on the boundary).  Diffusion: harmonic-mean face coefficients, boundary
+// faces kappa_p / h^2; convection (vel, or null): first-order upwind.
+__global__ void k_face_coef(int n, const double* kap, const double* vel, double shift, double* coef) {
   const long N = (long)n * n * n;
   const int m = n * n;
-  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h), ih = 1.0 / h;
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x) {
-    int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / m);
-    double kp = kap[p];
+    const int ci[3] = {(int)(p % n), (int)((p / n) % n), (int)(p / m)};
+    const long st[3] = {1, n, m};
+    const double kp = kap[p];
     double d = shift;
-    double cx = 0, cy = 0, cz = 0;
-    d += (x > 0) ? harm(kp, kap[p - 1], ih2) : kp * ih2;
-    if (x < n - 1) { cx = harm(kp, kap[p + 1], ih2); d += cx; } else d += kp * ih2;
-    d += (y > 0) ? harm(kp, kap[p - n], ih2) : kp * ih2;
-    if (y < n - 1) { cy = harm(kp, kap[p + n], ih2); d += cy; } else d += kp * ih2;
-    d += (z > 0) ? harm(kp, kap[p - m], ih2) : kp * ih2;
-    if (z < n - 1) { cz = harm(kp, kap[p + m], ih2); d += cz; } else d += kp * ih2;
+    for (int ax = 0; ax < 3; ++ax) {
+      const double be = vel ? vel[ax * N + p] : 0.0;
+      d += fabs(be) * ih;
+      for (int sg = 0; sg < 2; ++sg) {
+        const bool plus = sg == 1;
+        const bool in = plus ? ci[ax] < n - 1 : ci[ax] > 0;
+        double w = 0.0;
+        if (in) {
+          const double c = harm(kp, kap[plus ? p + st[ax] : p - st[ax]], ih2);
+          d += c;
+          w = c + upw(be, plus, ih);
+        } else {
+          d += kp * ih2;
+        }
+        coef[(1 + 2 * ax + sg) * N + p] = w;
+      }
+    }
     coef[p] = d;
-    coef[N + p] = cx;
-    coef[2 * N + p] = cy;
-    coef[3 * N + p] = cz;
   }
 }
-void face_coefficients(Ctx& c, int n, const double* kappa, double shift, double* coef) {
+void face_coefficients(Ctx& c, int n, const double* kappa, const double* vel, double shift, double* coef) {
   long N = (long)n * n * n;
   c.kbegin();
-  k_face_coef<<<nblk(N), 256, 0, c.st>>>(n, kappa, shift, coef);
-  c.kend(KC_STENCIL, 0, 5.0 * 8.0 * N);
+  k_face_coef<<<nblk(N), 256, 0, c.st>>>(n, kappa, vel, shift, coef);
+  c.kend(KC_STENCIL, 0, (vel ? 11.0 : 8.0) * 8.0 * N);
 }
 
-// out = alpha * A x + beta * y; optional per-column partial sums of out^2 and y^2.
+// out = alpha * A x + beta * y (trans: A^T x); optional per-column partial
+// sums of out^2 and y^2.  Row p of A^T takes, from the neighbour q = p + e,
+// the weight of row q toward p (direction -e).
 __global__ void k_stencil(int n, int nrhs, const double* __restrict__ coef, const double* __restrict__ x, long ld,
-                          const double* y, double* out, double alpha, double beta, double* part) {
+                          const double* y, double* out, double alpha, double beta, double* part, int trans) {
   const long N = (long)n * n * n;
   const int m = n * n;
   const int col = blockIdx.y;
@@ -398,14 +437,20 @@ __global__ void k_stencil(int n, int nrhs, const double* __restrict__ coef, cons
   double a1 = 0, a2 = 0;
   const double* xc = x + (long)col * ld;
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < N; p += (long)gridDim.x * blockDim.x) {
-    int xi = (int)(p % n), yi = (int)((p / n) % n), zi = (int)(p / m);
+    const int ci[3] = {(int)(p % n), (int)((p / n) % n), (int)(p / m)};
+    const long st[3] = {1, n, m};
     double v = coef[p] * xc[p];
-    if (xi < n - 1) v -= coef[N + p] * xc[p + 1];
-    if (xi > 0) v -= coef[N + p - 1] * xc[p - 1];
-    if (yi < n - 1) v -= coef[2 * N + p] * xc[p + n];
-    if (yi > 0) v -= coef[2 * N + p - n] * xc[p - n];
-    if (zi < n - 1) v -= coef[3 * N + p] * xc[p + m];
-    if (zi > 0) v -= coef[3 * N + p - m] * xc[p - m];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      if (ci[ax] > 0) {
+        const long q = p - st[ax];
+        v -= (trans ? coef[(2 + 2 * ax) * N + q] : coef[(1 + 2 * ax) * N + p]) * xc[q];
+      }
+      if (ci[ax] < n - 1) {
+        const long q = p + st[ax];
+        v -= (trans ? coef[(1 + 2 * ax) * N + q] : coef[(2 + 2 * ax) * N + p]) * xc[q];
+      }
+    }
     double yv = (beta != 0.0) ? y[(long)col * ld + p] : 0.0;
     double o = alpha * v + beta * yv;
     out[(long)col * ld + p] = o;
@@ -445,14 +490,14 @@ __global__ void k_reduce_pairs(int nrhs, int nparts, const double* part, double*
 }
 
 void stencil_apply(Ctx& c, int n, int nrhs, const double* coef, const double* x, long ld, const double* y,
-                   double* out, double alpha, double beta, double* norms_out) {
+                   double* out, double alpha, double beta, double* norms_out, bool trans) {
   long N = (long)n * n * n;
   int nb = (int)std::min<long>((N + 255) / 256, 1024);
   double* part = nullptr;
   if (norms_out) part = c.alloc<double>((size_t)nb * nrhs * 2);
   c.kbegin();
-  k_stencil<<<dim3(nb, nrhs), 256, 0, c.st>>>(n, nrhs, coef, x, ld, y, out, alpha, beta, part);
-  c.kend(KC_STENCIL, 13.0 * N * nrhs, 8.0 * (4.0 * N + N * nrhs * (2.0 + (beta != 0.0))));
+  k_stencil<<<dim3(nb, nrhs), 256, 0, c.st>>>(n, nrhs, coef, x, ld, y, out, alpha, beta, part, trans ? 1 : 0);
+  c.kend(KC_STENCIL, 15.0 * N * nrhs, 8.0 * (7.0 * N + N * nrhs * (2.0 + (beta != 0.0))));
   if (norms_out) {
     c.kbegin();
     k_reduce_pairs<<<nrhs, 256, 0, c.st>>>(nrhs, nb, part, norms_out);
@@ -469,7 +514,7 @@ void stencil_norms_scratch(cudaStream_t st, int n, int nrhs, const double* coef,
                            const double* y, double* out, double* part, int nb_max, double* pairs) {
   long N = (long)n * n * n;
   int nb = (int)std::min<long>((N + 255) / 256, nb_max);
-  k_stencil<<<dim3(nb, nrhs), 256, 0, st>>>(n, nrhs, coef, x, ld, y, out, -1.0, 1.0, part);
+  k_stencil<<<dim3(nb, nrhs), 256, 0, st>>>(n, nrhs, coef, x, ld, y, out, -1.0, 1.0, part, 0);
   k_reduce_pairs<<<nrhs, 256, 0, st>>>(nrhs, nb, part, pairs);
 }
 
@@ -629,7 +674,8 @@ void exp_inplace(Ctx& c, double* p, long n) {
   template void copy2d<T>(Ctx&, int, long, int, T, const T*, long, long, T*, long, long);                \
   template void set_identity_clusters<T>(Ctx&, int, int, int, T*, long, long);                           \
   template int batched_inverse<T>(Ctx&, int, int, T*, long);                                             \
-  template void assemble_level0<T>(Ctx&, const Geometry&, const double*, double, const int*, const int*, \
+  template void assemble_level0<T>(Ctx&, const Geometry&, const double*, const double*, double, const int*, \
+                                   const int*,                                                           \
                                    const std::vector<const int*>&, const std::vector<const int*>&,       \
                                    HMat<T>, HMat<T>, HMat<T>);                                           \
   template void permute_in<T>(Ctx&, int, int, const double*, long, const int*, T*);                      \

@@ -27,6 +27,7 @@ __all__ = [
     "point_source",
     "random_directions",
     "helmholtz_omega",
+    "vortex_velocity",
 ]
 
 
@@ -114,3 +115,22 @@ def helmholtz_omega(n: int, points_per_wavelength: float = 10.0) -> float:
             break
         omega *= 1.005
     return float(omega)
+
+
+def vortex_velocity(n: int, alpha: float, a: float = 1.0) -> np.ndarray:
+    """Convection velocity ``alpha * b(x)`` of the convection-diffusion problem
+    (Section 5, Eq. codi) at the nodes, shape ``(3, n^3)`` (planar x, y, z
+    components in the node order above).  ``b`` is the paper's three-dimensional
+    vortex field; its frequency ``a`` is not given in the paper (read as 1).
+    """
+    t = 2.0 * np.pi * a
+    c = node_coords_1d(n)
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")  # [k][j][i]
+    sx, cx = np.sin(t * x), np.cos(t * x)
+    sy, cy = np.sin(t * (0.125 + y)), np.cos(t * (0.125 + y))
+    sz8, cz8 = np.sin(t * (0.125 + z)), np.cos(t * (0.125 + z))
+    sz, cz = np.sin(t * z), np.cos(t * z)
+    bx = sx * sy + sz8 * sx
+    by = cx * cy + cy * cz
+    bz = cx * cz8 + sy * sz
+    return alpha * np.stack([bx.ravel(), by.ravel(), bz.ravel()], axis=0)

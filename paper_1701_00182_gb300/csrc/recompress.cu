@@ -825,7 +825,10 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     size_t sm = 2 * (size_t)r * sizeof(T);
     if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_pchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     c.kbegin();
-    k_pchol<T><<<(unsigned)(2 * NB), kCholThreads, sm, c.st>>>(r, G.p, T(epsd), R.p, piv.p, kk.p);
+    // one thread per Gram column (64 .. 1024): small blocks at deep levels do
+    // not pay for idle warps in every per-pivot barrier
+    const int thr = std::min(kCholThreads, std::max(64, (r + 31) / 32 * 32));
+    k_pchol<T><<<(unsigned)(2 * NB), thr, sm, c.st>>>(r, G.p, T(epsd), R.p, piv.p, kk.p);
     c.kend(KC_PCHOL, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r);
   }
   // Ranks of the two factorisations: the core only needs its leading
@@ -864,7 +867,8 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
       size_t sm2 = base2 + (size_t)se2 * sizeof(T);
       ACR_CUDA(cudaFuncSetAttribute(k_qrcp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
       c.kbegin();
-      k_qrcp<T><<<(unsigned)NB, kQrcpThreads, sm2, c.st>>>(r, Cc.p, kk.p, NB, W.p, Xo.p, Yo.p, sig.p, rank.p, T(tol),
+      const int thr = std::min(kQrcpThreads, std::max(64, (8 * std::max(kmaxL, kmaxR) + 31) / 32 * 32));
+      k_qrcp<T><<<(unsigned)NB, thr, sm2, c.st>>>(r, Cc.p, kk.p, NB, W.p, Xo.p, Yo.p, sig.p, rank.p, T(tol),
                                                            se2, c.d_jflops);
       c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r);
     } else {

@@ -40,7 +40,15 @@ __global__ void k_copy2d(int P, long rows, int cols, T alpha, const T* src, long
     const long p = rw / rows, i = rw - p * rows;
     const T* sr = src + p * sps + i * sld;
     T* dr = dst + p * dps + i * dld;
-    for (int j = lane; j < cols; j += 32) dr[j] = alpha * sr[j];
+    int j = lane;
+    for (; j + 96 < cols; j += 128) {  // four loads in flight per lane
+      const T a0 = sr[j], a1 = sr[j + 32], a2 = sr[j + 64], a3 = sr[j + 96];
+      dr[j] = alpha * a0;
+      dr[j + 32] = alpha * a1;
+      dr[j + 64] = alpha * a2;
+      dr[j + 96] = alpha * a3;
+    }
+    for (; j < cols; j += 32) dr[j] = alpha * sr[j];
   }
 }
 template <class T>

@@ -27,3 +27,21 @@ def test_helmholtz_points_per_wavelength():
     w = synthetic.helmholtz_omega(n)
     ppw = 2 * np.pi / (w / (n + 1))
     assert 9.5 < ppw <= 10.0
+
+
+def test_vortex_velocity_is_divergence_free():
+    """The vortex field of Eq. codi is solenoidal: its six cross terms cancel in
+    pairs, and on the node grid the central-difference divergence cancels to
+    rounding (each component is a product of per-axis factors).  A changed sign,
+    phase or factor in any component breaks the cancellation."""
+    n = 31
+    h = synthetic.grid_h(n)
+    v = synthetic.vortex_velocity(n, 1.0).reshape(3, n, n, n)  # [component][k][j][i]
+    div = (
+        (v[0][1:-1, 1:-1, 2:] - v[0][1:-1, 1:-1, :-2])
+        + (v[1][1:-1, 2:, 1:-1] - v[1][1:-1, :-2, 1:-1])
+        + (v[2][2:, 1:-1, 1:-1] - v[2][:-2, 1:-1, 1:-1])
+    ) / (2 * h)
+    assert np.abs(div).max() < 1e-11 * np.abs(v).max() / h
+    assert np.abs(v).max() > 1.0  # and the field is not trivially zero
+    assert np.allclose(synthetic.vortex_velocity(n, 7.0), 7.0 * synthetic.vortex_velocity(n, 1.0))

@@ -67,8 +67,9 @@ typedef struct {
   void* cuda_stream;      /* cudaStream_t to run on; NULL = legacy default stream */
   int profile;            /* 1 = time every kernel launch with CUDA events (per-class totals in acr_stats) */
   int inverse_fp64;       /* ACR_FP32 only: 1 = leaf and Woodbury-coupling inverses computed in FP64 */
-  int tensor_cores;       /* ACR_FP32 only: 1 = large GEMM tiles on the tensor pipe with a 3xTF32 split
-                             (FP32-level accuracy) instead of FP32 FMA */
+  int tensor_cores;       /* ACR_FP32 only: 1 = GEMM tiles and the fused HODLR expansion on the tcgen05
+                             tensor cores with a 3xTF32 split (FP32-level accuracy; large products
+                             through TMA-fed pre-split tiles) instead of FP32 FMA tiles */
   int core_svd;           /* truncation of the recompression core: 0 = auto (rank-revealing QR with column
                              pivoting for ACR_FP32, one-sided Jacobi SVD for ACR_FP64), 1 = Jacobi SVD,
                              2 = pivoted QR */

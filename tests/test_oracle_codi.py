@@ -89,3 +89,32 @@ def test_block_cr_solves_the_nonsymmetric_system():
     u = cr.cr_solve_system(n, D, E, F, f)
     ref = spla.spsolve(op.assemble(n, None, 0.0, v).tocsc(), f)
     assert np.linalg.norm(u - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_direction_pin_rejects_a_downwind_operator(monkeypatch):
+    """Plant the most plausible mistake (differencing toward the downstream
+    neighbour: the two upwind weights swapped) in the oracle and check that
+    the quadratic test above fails for it while the real operator passes."""
+    n = 9
+    h = 1.0 / (n + 1)
+    v = synthetic.vortex_velocity(n, 20.0)
+    c = (np.arange(n) + 1.0) * h
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    u = (x ** 2).ravel()
+    bx = v[0].reshape(n, n, n)
+    want = -2.0 + bx * (2.0 * x - np.sign(bx) * h)
+    inner = (slice(1, n - 1),) * 3
+
+    def miss(apply_fn):
+        Au = apply_fn(n, None, u, 0.0, v).reshape(n, n, n)
+        return np.abs(Au[inner] - want[inner]).max()
+
+    assert miss(op.apply) < 1e-9
+    real = op.upwind_weights
+
+    def downwind(n_, velocity):
+        dplus, wminus, wplus = real(n_, velocity)
+        return dplus, wplus, wminus
+
+    monkeypatch.setattr(op, "upwind_weights", downwind)
+    assert miss(op.apply) > 1.0  # off by 2 |beta_x| h at the inner nodes

@@ -53,7 +53,6 @@ struct Ctx {
   long long gemm_flops = 0;
   size_t live_bytes = 0, peak_bytes = 0, budget = 0;
   bool autotune = false;
-  std::vector<std::pair<unsigned long long, int>> tuned;  // shape key -> config
   std::map<uintptr_t, size_t> live;  // allocation start -> bytes (for the operand extent check)
   bool check_bounds = false;  // ACR_CHECK_BOUNDS=1: verify every GEMM operand range on the host
   bool inverse_fp64 = false;  // FP32 factorisation: leaf and coupling inverses in FP64

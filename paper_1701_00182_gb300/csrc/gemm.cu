@@ -674,9 +674,13 @@ int split_for(int cfg, int M, int N, int K, long batch) {
 std::mutex g_tune_mu;
 std::vector<std::pair<unsigned long long, int>> g_tuned;
 
-unsigned long long shape_key(int es, int M, int N, int K, long batch) {
+// Tuning cache key: element size, tensor-core permission and the log2 classes
+// of the shape (a handle that forbids the tensor cores never reuses a choice
+// made by one that allows them).
+unsigned long long shape_key(int es, bool tensor, int M, int N, int K, long batch) {
   auto lg = [](long v) { int b = 0; while (v > 1) { v >>= 1; ++b; } return (unsigned long long)b; };
-  return (unsigned long long)es | (lg(M) << 8) | (lg(N) << 16) | (lg(K) << 24) | (lg(batch) << 32);
+  return (unsigned long long)es | (lg(M) << 8) | (lg(N) << 16) | (lg(K) << 24) | (lg(batch) << 32) |
+         ((unsigned long long)(tensor ? 1 : 0) << 48);
 }
 
 }  // namespace
@@ -774,7 +778,7 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
     cfg = c.force_cfg;
     split = split_for(cfg, M, N, K, batch);
   } else if (c.autotune) {
-    unsigned long long key = shape_key(sizeof(T), M, N, K, batch);
+    unsigned long long key = shape_key(sizeof(T), c.tensor, M, N, K, batch);
     int found = -1;
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);

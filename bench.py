@@ -8,10 +8,17 @@ One step = acr_factor in FP32 + FP64 iterative refinement (ACR as the
 preconditioner) until every column has ||b - A x|| / ||b|| <= 1e-10.
 Metric: DOF/s = N * nrhs / (factor + solve seconds) -- higher is better.
 
+The headline steps run without per-kernel timing; a separate profiled pass of
+the same step (CUDA events around every launch on the library's stream) gives
+the per-kernel-class table and the roofline of the dominant class.  The FP64
+comparator (plain FP64 ACR + FP64 refinement, same leaf and tolerance) is one
+more step after the timed region.
+
 ``--impl reference`` times the CPU FP64 oracle (conjugate gradients on the
-same operator and RHS, host cores) on a bounded sample of the same workload.
-Multi-GPU: replicas only (every rank solves its own copy; no collective on the
-data path); the value is the sum over ranks.
+same operator and RHS, host cores, threaded sparse products) on bounded
+samples of the same workload.  Multi-GPU: replicas only (every rank solves
+its own copy; no collective on the data path); the value is the sum over
+ranks.
 """
 from __future__ import annotations
 
@@ -116,41 +123,65 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cg_sample(n, g, f, rtol, budget_s):
-    """Oracle FP64 CG on one RHS with a wall-time budget; returns (DOF/s, description)."""
+def threaded_operator(A, threads):
+    """The oracle's sparse matrix as a LinearOperator whose products run on
+    `threads` host threads, one block of rows each (SciPy's sparse product
+    releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import scipy.sparse.linalg as spla
+
+    A = A.tocsr()
+    N = A.shape[0]
+    bounds = np.linspace(0, N, threads + 1).astype(np.int64)
+    parts = [A[bounds[i]:bounds[i + 1]] for i in range(threads)]
+    pool = ThreadPoolExecutor(threads)
+
+    def mv(x):
+        x = np.ravel(x)
+        out = np.empty(N)
+
+        def one(i):
+            out[bounds[i]:bounds[i + 1]] = parts[i] @ x
+
+        list(pool.map(one, range(threads)))
+        return out
+
+    return spla.LinearOperator((N, N), matvec=mv, dtype=np.float64)
+
+
+def cpu_converged(n, g, f, rtol, threads=None):
+    """The oracle's FP64 CG on one right-hand side, run to convergence on the
+    host cores; returns a dict with the measured time and iteration count."""
     from oracle import iterative, operator as op
 
-    A = op.assemble(n, g)
-    u = np.zeros_like(f)
-    r = f.copy()
-    p = r.copy()
-    rr = r @ r
-    f2 = f @ f
+    threads = threads or os.cpu_count() or 1
+    A = threaded_operator(op.assemble(n, g), threads)
     t0 = time.perf_counter()
-    it = 0
-    while True:
-        it += 1
-        Ap = A @ p
-        alpha = rr / (p @ Ap)
-        u += alpha * p
-        r -= alpha * Ap
-        rr_new = r @ r
-        if rr_new <= rtol * rtol * f2:
-            break
-        p = r + (rr_new / rr) * p
-        rr = rr_new
-        if time.perf_counter() - t0 > budget_s:
-            break
+    u, it = iterative.cg(A, f, rtol=rtol, maxiter=50000)
     t = time.perf_counter() - t0
-    relres = float(np.sqrt(rr_new / f2))
-    if relres <= rtol:
-        t_full, kind = t, "converged"
-    else:
-        t_full = t * np.log(rtol) / np.log(relres)
-        kind = "extrapolated from rel. residual %.2e after %d iterations" % (relres, it)
-    del iterative
-    return n ** 3 / t_full, ("oracle FP64 CG (not ACR), n=%d, one RHS (seed 100) to %.0e: %d iterations in %.1f s, %s"
-                            % (n, rtol, it, t, kind)), t_full
+    relres = float(iterative.rel_residual(n, g, u, f)[0])
+    return {"seconds": t, "iters": it, "rel_residual": relres, "threads": threads, "A": A,
+            "converged": relres <= rtol * 1.01}
+
+
+def cpu_chunk(A, f, iters):
+    """Seconds for `iters` iterations of the oracle's CG (no early stop)."""
+    from oracle import iterative
+
+    t0 = time.perf_counter()
+    iterative.cg(A, f, rtol=0.0, maxiter=iters)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_record(n, conv, rtol):
+    N = n ** 3
+    desc = ("oracle FP64 CG (not ACR), n=%d, one RHS (seed 100): %d iterations to rel. residual %.1e "
+            "(measured %.2e, %s) in %.1f s; sparse products on %d host threads"
+            % (n, conv["iters"], rtol, conv["rel_residual"], "converged" if conv["converged"] else "NOT converged",
+               conv["seconds"], conv["threads"]))
+    return {"value": N / conv["seconds"], "unit": "DOF/s", "cores": os.cpu_count(), "threads": conv["threads"],
+            "kind": "oracle", "sample": desc}
 
 
 def reference_main(args):
@@ -160,56 +191,100 @@ def reference_main(args):
     n = WORKLOAD["n"]
     g = synthetic.gaussian_random_field(n, WORKLOAD["kappa_seed"])
     f = synthetic.uniform_rhs(n, 100)
+    conv = cpu_converged(n, g, f, WORKLOAD["rtol"])
+    # Each step: a bounded chunk of the same CG run (about ref_budget seconds),
+    # scaled by the measured iteration count to 1e-10.
+    per_it = conv["seconds"] / max(conv["iters"], 1)
+    chunk = int(max(20, min(conv["iters"], args.ref_budget / per_it)))
     vals = []
-    desc = ""
     for s in range(args.warmup + args.steps):
-        v, desc, _ = cg_sample(n, g, f, WORKLOAD["rtol"], args.ref_budget)
+        t = cpu_chunk(conv["A"], f, chunk)
         if s >= args.warmup:
-            vals.append(v)
+            vals.append(WORKLOAD["N"] / (t * conv["iters"] / chunk))
     value = float(np.median(vals))
+    cpu = cpu_baseline_record(n, conv, WORKLOAD["rtol"])
+    cpu["value"] = value
+    cpu["sample"] += ("; each timed step: %d iterations of the same CG, time scaled by %d/%d iterations"
+                      % (chunk, conv["iters"], chunk))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": WORKLOAD["N"] * WORKLOAD["nrhs"] / value * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": WORKLOAD,
-        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "config": WORKLOAD, "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
 
 
-def roofline(kernels, precision, peaks, source):
-    name, kc = max(kernels.items(), key=lambda kv: kv[1]["ms"])
+# Kernel classes of the library's profile and the roof each is reported against.
+TENSOR_CLASSES = ("gemm_tcgen05", "hodlr_expand")
+ALU_CLASSES = ("gemm", "householder_qr", "pivoted_cholesky", "core_truncation", "rebuild_coef", "gauss_jordan")
+
+
+def peaks_for(precision, peaks, source):
+    """(tensor, alu, hbm) ceilings and their provenance."""
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    # FP32 products as three TF32 MMAs each: the tensor-pipe ceiling in FP32
+    # flops is the TF32 dense rate / 3; TF32 = measured sustained BF16 x the
+    # nominal TF32 : BF16 ratio (1.1 : 2.25 PFLOP/s dense).
+    tensor = peaks["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
+    alu = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12 if precision == "f32" else 1.25
+    return {
+        "tensor": (tensor, "%s bf16_tflops_sustained x 1.1/2.25 (TF32) / 3 (3xTF32 passes)" % source),
+        "alu": (alu, "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz if precision == "f32"
+                else "nominal FP64 rate of the recipe"),
+        "hbm": (peaks["hbm_gbs"], "%s hbm_gbs" % source),
+    }
+
+
+def class_roof(name, kc, precision, peaks, source):
+    """Roofline entry of one kernel class: achieved rate against its bound."""
     ms = kc["ms"]
     if ms <= 0:
-        return None, name
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12 if precision == "f32" else 1.25  # TFLOP/s
-    hbm = peaks["hbm_gbs"]
+        return None
+    roofs = peaks_for(precision, peaks, source)
     gbs = kc["bytes"] / (ms * 1e-3) / 1e9
     tfs = kc["flops"] / (ms * 1e-3) / 1e12
     ai = kc["flops"] / kc["bytes"] if kc["bytes"] else 0.0
-    ridge = alu_peak * 1e12 / (hbm * 1e9)
-    per_launch = kc["bytes"] / max(kc["launches"], 1)
-    if name == "gemm_tcgen05":
-        # FP32 products as three TF32 MMAs each: the tensor-pipe ceiling in FP32
-        # flops is the TF32 dense rate / 3; TF32 = measured sustained BF16 x the
-        # nominal TF32 : BF16 ratio (1.1 : 2.25 PFLOP/s dense).
-        tf32 = peaks["bf16_tflops_sustained"] * (1.1 / 2.25)
-        peak = tf32 / 3.0
-        out = {"bound": "tensor", "achieved": tfs, "peak": peak, "unit": "TFLOP/s", "frac": tfs / peak,
-               "peak_source": "%s bf16_tflops_sustained x 1.1/2.25 (TF32) / 3 (3xTF32 passes)" % source}
-    elif kc["flops"] > 0 and ai >= ridge:
-        out = {"bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfs / alu_peak,
-               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz
-               if precision == "f32" else "nominal FP64 rate of the recipe"}
+    ridge = roofs["alu"][0] * 1e12 / (roofs["hbm"][0] * 1e9)
+    if name in TENSOR_CLASSES and precision == "f32":
+        bound = "tensor"
+    elif kc["flops"] > 0 and (name in ALU_CLASSES or ai >= ridge):
+        bound = "alu"
     else:
-        out = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-               "peak_source": "%s hbm_gbs" % source}
-    out.update({"kernel": name, "traffic": None, "algorithmic_bytes_per_launch": per_launch,
-                "launches": kc["launches"], "share_of_device_time": None, "arith_intensity": ai})
+        bound = "hbm"
+    peak, src = roofs[bound]
+    ach = gbs if bound == "hbm" else tfs
+    return {"bound": bound, "achieved": ach, "peak": peak, "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
+            "frac": ach / peak, "peak_source": src, "ms": ms, "launches": kc["launches"],
+            "algorithmic_bytes_per_launch": kc["bytes"] / max(kc["launches"], 1),
+            "algorithmic_flops_per_launch": kc["flops"] / max(kc["launches"], 1),
+            "hbm_frac": gbs / roofs["hbm"][0], "arith_intensity": ai}
+
+
+def roofline(kernels, precision, peaks, source):
+    """Roofline of the dominant kernel class (largest device time)."""
+    name, kc = max(kernels.items(), key=lambda kv: kv[1]["ms"])
+    out = class_roof(name, kc, precision, peaks, source)
+    if out is None:
+        return None, name
+    out.update({"kernel": name, "traffic": None, "share_of_device_time": None})
     return out, name
+
+
+def class_table(kernels, precision, peaks, source):
+    """Every kernel class with device time, its share and its roofline fraction."""
+    tot = sum(v["ms"] for v in kernels.values()) or 1.0
+    table = {}
+    for name, kc in sorted(kernels.items(), key=lambda kv: -kv[1]["ms"]):
+        e = class_roof(name, kc, precision, peaks, source)
+        if e is None:
+            continue
+        table[name] = {"share": kc["ms"] / tot, "ms": round(kc["ms"], 3), "launches": kc["launches"],
+                       "bound": e["bound"], "achieved": round(e["achieved"], 3), "unit": e["unit"],
+                       "frac": round(e["frac"], 4), "hbm_frac": round(e["hbm_frac"], 4)}
+    return table
 
 
 def main():
@@ -223,8 +298,9 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--fp64-compare", type=int, default=0, help="also time one FP64 ACR step (comparator)")
-    ap.add_argument("--ref-budget", type=float, default=20.0, help="seconds of CPU work per oracle sample")
+    ap.add_argument("--fp64-compare", type=int, default=1, help="also time one FP64 ACR step (the comparator)")
+    ap.add_argument("--profile-steps", type=int, default=2, help="separate profiled steps for the class table")
+    ap.add_argument("--ref-budget", type=float, default=4.0, help="seconds of CPU work per reference-arm step")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e", type=int, default=1, help="also time the end-to-end host-buffer path")
     args = ap.parse_args()
@@ -266,10 +342,10 @@ def main():
     X = torch.zeros_like(B)
     prec = acr.ACR_FP32 if args.precision == "f32" else acr.ACR_FP64
 
-    def step(profile=0, kappa=g_dev, b=B, x=X, precision=prec):
+    def step(profile=0, kappa=g_dev, b=B, x=X, precision=prec, **kw):
+        kw.setdefault("autotune", args.autotune)
         h = acr.acr_factor(n, kappa, WORKLOAD["tol"], WORKLOAD["leaf"], precision=precision, profile=profile,
-                           nrhs_max=nrhs, autotune=args.autotune, graphs=1,
-                           tensor_cores=args.tensor_cores)
+                           nrhs_max=nrhs, graphs=1, tensor_cores=args.tensor_cores, **kw)
         it, rel, st = acr.acr_solve_ir(h, b.T, x.T, rtol=WORKLOAD["rtol"], maxit=60, check=False)
         s = acr.acr_get_stats(h)
         h.close()
@@ -281,32 +357,45 @@ def main():
     if dist:
         dist.barrier()
     peaks, psrc = load_peaks()
-    kern = {}
     launches = 0
     iters = []
     worst = 0.0
     t_factor = 0.0
+    last = None
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(args.steps):
-            it, rel, st, s = step(profile=1)
+            it, rel, st, s = step()
             iters.append(it)
             worst = max(worst, float(np.max(rel)))
             launches += sum(v["launches"] for v in s["kernels"].values())
             t_factor += s["t_factor_ms"]
-            for k, v in s["kernels"].items():
-                acc = kern.setdefault(k, {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 0})
-                for f in acc:
-                    acc[f] += v[f]
+            last = s
         e1.record()
         torch.cuda.synchronize()
     clocks = clk.summary()
     ms = e0.elapsed_time(e1) / args.steps
     ms = reduce_step_time(ms, world, dist, "cuda")
     value = aggregate_value(world, N, nrhs, ms)
+
+    # Per-kernel-class profile: the same step with CUDA events around every
+    # launch (on the library's stream), kept out of the headline timing.
+    kern = {}
+    prof_ms = None
+    if args.profile_steps > 0:
+        torch.cuda.synchronize()
+        p0 = time.perf_counter()
+        for _ in range(args.profile_steps):
+            _, _, _, s = step(profile=1)
+            for k, v in s["kernels"].items():
+                acc = kern.setdefault(k, {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 0})
+                for f in acc:
+                    acc[f] += v[f] / args.profile_steps
+        torch.cuda.synchronize()
+        prof_ms = (time.perf_counter() - p0) / args.profile_steps * 1e3
 
     # end-to-end through the C ABI: host kappa and pinned host RHS, result read back every step
     e2e = None
@@ -325,24 +414,30 @@ def main():
         e2e = {"value": world * N * nrhs / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": 8 * N * (nrhs + 1),
                "d2h_bytes_per_step": 8 * N * nrhs}
 
-    rl, dom = roofline(kern, args.precision, peaks, psrc)
-    tot_ms = sum(v["ms"] for v in kern.values())
-    if rl:
-        rl["share_of_device_time"] = kern[dom]["ms"] / tot_ms if tot_ms else None
+    rl, classes = None, None
+    if kern:
+        rl, dom = roofline(kern, args.precision, peaks, psrc)
+        classes = class_table(kern, args.precision, peaks, psrc)
+        if rl:
+            rl["share_of_device_time"] = classes[dom]["share"]
     fp64 = None
-    if args.fp64_compare and args.precision == "f32":
+    if args.fp64_compare and args.precision == "f32" and rank == 0:
+        # plain FP64 ACR with its fastest correct settings: pivoted-QR core
+        # truncation, heuristic GEMM tilings (FP64 autotuning costs minutes)
         torch.cuda.synchronize()
         ta = time.perf_counter()
-        it64, rel64, st64, s64 = step(precision=acr.ACR_FP64)
+        it64, rel64, st64, s64 = step(precision=acr.ACR_FP64, core_svd=2, autotune=0)
         torch.cuda.synchronize()
         t64 = time.perf_counter() - ta
         fp64 = {"s_per_step": t64, "value": N * nrhs / t64, "unit": "DOF/s", "t_factor_s": s64["t_factor_ms"] / 1e3,
-                "ir_iters": it64, "max_rel_residual": float(np.max(rel64)), "status": st64,
-                "max_rank_top": max(max(r) for r in s64["max_rank"])}
+                "t_solve_s": t64 - s64["t_factor_ms"] / 1e3, "ir_iters": it64,
+                "max_rel_residual": float(np.max(rel64)), "status": st64, "core_truncation": "pivoted QR",
+                "max_rank_by_cr_level": [max(r) for r in s64["max_rank_d"]],
+                "mixed_speedup": value / world / (N * nrhs / t64)}
     cpu = None
     if args.cpu_baseline and rank == 0:
-        v, desc, _ = cg_sample(n, g_host, F_host[:, 0].copy(), WORKLOAD["rtol"], args.ref_budget)
-        cpu = {"value": v, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": desc}
+        conv = cpu_converged(n, g_host, F_host[:, 0].copy(), WORKLOAD["rtol"])
+        cpu = cpu_baseline_record(n, conv, WORKLOAD["rtol"])
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
@@ -351,7 +446,10 @@ def main():
             "t_factor_s": t_factor / args.steps / 1e3, "t_solve_s": ms / 1e3 - t_factor / args.steps / 1e3,
             "ir_iters": iters, "max_rel_residual": worst, "gpu_launches": launches, "clocks": clocks,
             "e2e": e2e, "roofline": rl, "cpu_baseline": cpu, "fp64_acr": fp64,
-            "kernel_ms": {k: round(v["ms"], 3) for k, v in kern.items()},
+            "max_rank_by_cr_level": [max(r) for r in last["max_rank_d"]] if last else None,
+            "max_rank_d": last["max_rank_d"] if last else None,
+            "factor_bytes": last["factor_bytes"] if last else None,
+            "profiled_ms_per_step": prof_ms, "classes": classes,
         }
         print(json.dumps(line))
     if dist:

@@ -70,9 +70,8 @@ typedef struct {
   int tensor_cores;       /* ACR_FP32 only: 1 = GEMM tiles and the fused HODLR expansion on the tcgen05
                              tensor cores with a 3xTF32 split (FP32-level accuracy; large products
                              through TMA-fed pre-split tiles) instead of FP32 FMA tiles */
-  int core_svd;           /* truncation of the recompression core: 0 = auto (rank-revealing QR with column
-                             pivoting for ACR_FP32, one-sided Jacobi SVD for ACR_FP64), 1 = Jacobi SVD,
-                             2 = pivoted QR */
+  int core_svd;           /* truncation of the recompression core: 0 = default (rank-revealing QR with
+                             column pivoting, both precisions), 1 = one-sided Jacobi SVD, 2 = pivoted QR */
   int coarse_dense_max;   /* coarsest plane factorised densely in FP64 when n^2 <= this (0 = default 4096,
                              negative = never; otherwise it is inverted as a HODLR matrix) */
   int graphs;             /* 1 = capture the solve sweeps once per (nrhs, transpose) as a CUDA graph and replay
@@ -165,9 +164,11 @@ int acr_residual(acr_handle h, const double* b, const double* x, double* r, int 
  * The call allocates nothing: its reduction scratch is a fixed ~1 MiB array
  * in device memory that every GPU using the library holds until the process
  * exits.  The first call on each device looks up that array's device address
- * (with the device current), so make the first call on a device before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * (other streams, other threads) race and must be serialised by the caller.
+ * (with that device current).  The call waits for the handle's stream (it
+ * reads the norms back), so it must not be made while that stream is being
+ * captured into a CUDA graph.  All calls share the array: calls that overlap
+ * on the GPU (other streams, other threads) race and must be serialised by
+ * the caller.  A failed launch returns ACR_ERR_CUDA.
  */
 int acr_residual_noalloc(acr_handle h, const double* b, const double* x, double* r, int nrhs, long ld,
                          double* rel_norms);
@@ -187,8 +188,10 @@ int acr_solve_ir(acr_handle h, const double* b, double* x, int nrhs, long ld, do
 
 /*
  * acr_solve_ir_transpose -- refinement with the transpose solve:
- * x_0 = 0; repeat x += M^{-T}(b - A^T x).  The residual uses the 7-point
- * operator, which is symmetric, so A^T x = A x.  Arguments as acr_solve_ir.
+ * x_0 = 0; repeat x += M^{-T}(b - A^T x).  The FP64 residual applies the
+ * transposed 7-point stencil: for the diffusion operator A^T = A, and with
+ * opts.velocity set (non-symmetric upwind operator) it applies A^T, whose
+ * row p holds the couplings of column p of A.  Arguments as acr_solve_ir.
  */
 int acr_solve_ir_transpose(acr_handle h, const double* b, double* x, int nrhs, long ld, double rtol, int maxit,
                            int* iters, double* rel_res);

@@ -732,6 +732,17 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
       h->vel = DBuf<double>(c, 3 * N);
       ACR_CUDA(cudaMemcpyAsync(h->vel.p, o.velocity, 3 * N * sizeof(double), cudaMemcpyDefault, c.st));
     }
+    // Inputs the operator cannot be built from (kappa = exp(log_kappa) not a
+    // positive finite number, a non-finite velocity or shift) are argument errors.
+    if (!std::isfinite(o.shift)) throw AcrError(ACR_ERR_ARG, "shift is not finite");
+    flag_invalid(c, h->kappa.p, N, true, c.d_flag + 3);
+    if (h->vel.p) flag_invalid(c, h->vel.p, 3 * N, false, c.d_flag + 3);
+    {
+      int bad = 0;
+      ACR_CUDA(cudaMemcpyAsync(&bad, c.d_flag + 3, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+      ACR_CUDA(cudaStreamSynchronize(c.st));
+      if (bad) throw AcrError(ACR_ERR_ARG, "log_kappa or velocity holds NaN / infinite values");
+    }
     h->coef = DBuf<double>(c, 7 * N);
     face_coefficients(c, n, h->kappa.p, h->vel.p, o.shift, h->coef.p);
     std::memset(&h->stats, 0, sizeof(h->stats));

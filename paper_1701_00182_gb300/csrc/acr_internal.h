@@ -58,7 +58,7 @@ struct Ctx {
   bool inverse_fp64 = false;  // FP32 factorisation: leaf and coupling inverses in FP64
   bool tensor = false;        // FP32 GEMMs of large tiles on the tensor cores (3xTF32)
   int force_cfg = -1;         // ACR_GEMM_CFG=<i>: every GEMM uses tiling i where it is valid (debugging)
-  int core_svd = 0;           // core truncation: 0 auto (pivoted QR in FP32, Jacobi SVD in FP64), 1 Jacobi, 2 pivoted QR
+  int core_svd = 0;           // core truncation: 0 / 2 pivoted QR (default), 1 Jacobi SVD
   void check_range(const void* base, long lo, long hi, size_t es, const char* what) const;
   bool profile = false;  // record CUDA events around every launch, accumulated per kernel class
   double kc_ms[16] = {}, kc_flops[16] = {}, kc_bytes[16] = {};
@@ -214,6 +214,8 @@ void stencil_apply(Ctx& c, int n, int nrhs, const double* coef, const double* x,
                    double* out, double alpha, double beta, double* norms_out /*2*nrhs or null*/, bool trans = false);
 template <class T> void expand_leaves(Ctx& c, int m, int b, const T* leaf, T* dense);
 void exp_inplace(Ctx& c, double* p, long n);
+// Sets *flag (device int) if an entry of p is NaN / infinite (or, with positive, not > 0).
+void flag_invalid(Ctx& c, const double* p, long n, bool positive, int* flag);
 void stencil_norms_scratch(cudaStream_t st, int n, int nrhs, const double* coef, const double* x, long ld,
                            const double* y, double* out, double* part, int nb_max, double* pairs);
 void grad_logkappa(Ctx& c, int n, int nrhs, const double* kap, const double* u, const double* lam, long ld,

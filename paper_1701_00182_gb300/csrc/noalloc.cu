@@ -79,6 +79,9 @@ extern "C" int acr_residual_noalloc(acr_handle h, const double* b, const double*
   double* part = scratch;
   double* pairs = scratch + kPartElems;
   acr::stencil_norms_scratch(st, n, nrhs, coef, x, ld, b, r, part, kMaxBlocks, pairs);
+  // A failed launch must not fall through to reading the previous call's
+  // norms out of the shared array.
+  if (cudaGetLastError() != cudaSuccess) return ACR_ERR_CUDA;
   double hn[2 * kMaxRhs];
   if (cudaMemcpyAsync(hn, pairs, 2 * sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {

@@ -841,6 +841,11 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     kmaxL = std::max(kmaxL, hk[i]);
     kmaxR = std::max(kmaxR, hk[NB + i]);
   }
+  if (!qr) {  // pivoted Cholesky: step t updates r entries with t products each
+    double f = 0;
+    for (long i = 0; i < 2 * NB; ++i) f += (double)r * hk[i] * hk[i];
+    c.kc_flops[KC_PCHOL] += f;
+  }
   DBuf<T> Cc(c, NB * (size_t)r * r);
   {
     Op<T> A{R.p, r, 1, 0, (long)r * r, 0, 0, 0};
@@ -859,7 +864,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     int smem_elems = (int)std::min<size_t>((size_t)r * r, cap > base ? (cap - base) / sizeof(T) : 0);
     size_t sm = base + (size_t)smem_elems * sizeof(T);
     ACR_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    const bool use_qrcp = c.core_svd == 2 || (c.core_svd == 0 && sizeof(T) == 4);
+    const bool use_qrcp = c.core_svd != 1;
     if (use_qrcp) {
       size_t base2 = (size_t)r * (3 * sizeof(T) + sizeof(int)) + ((r & 1) ? sizeof(int) : 0);
       base2 = (base2 + 15) / 16 * 16;
@@ -916,7 +921,12 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     k_coef<T><<<grid, 256, sm, c.st>>>(r, Kout, NB, qr ? 1 : 0, R.p, piv.p, kk.p, Xo.p, Yo.p, sig.p, rank.p,
                                        scale.p, Z.p, Cw, gs, kmax);
   }
-  c.kend(KC_COEF, 0, 2.0 * NB * sizeof(T) * ((double)r * r + (double)r * Kout));
+  {  // back substitution: k^2 products per coefficient column, both sides
+    double f = 0;
+    if (!qr)
+      for (long i = 0; i < 2 * NB; ++i) f += (double)hk[i] * hk[i] * hr[i % NB];
+    c.kend(KC_COEF, f, 2.0 * NB * sizeof(T) * ((double)r * r + (double)r * Kout));
+  }
   Uout = DBuf<T>(c, (size_t)P * m * Kout);
   Vout = DBuf<T>(c, (size_t)P * m * Kout);
   for (int side = 0; side < 2; ++side) {

@@ -671,6 +671,22 @@ void expand_leaves(Ctx& c, int m, int b, const T* leaf, T* dense) {
 __global__ void k_exp_inplace(double* p, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) p[i] = exp(p[i]);
 }
+// flag = 1 if any entry is NaN or infinite (or, with positive, not > 0).
+__global__ void k_flag_invalid(const double* p, long n, int positive, int* flag) {
+  bool bad = false;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double v = p[i];
+    bad |= !isfinite(v) || (positive && !(v > 0.0));
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+void flag_invalid(Ctx& c, const double* p, long n, bool positive, int* flag) {
+  c.kbegin();
+  k_flag_invalid<<<nblk(n), 256, 0, c.st>>>(p, n, positive ? 1 : 0, flag);
+  c.kend(KC_ASSEMBLE, 0, 8.0 * n);
+}
+
 void exp_inplace(Ctx& c, double* p, long n) {
   c.kbegin();
   k_exp_inplace<<<nblk(n), 256, 0, c.st>>>(p, n);

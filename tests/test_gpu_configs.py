@@ -34,10 +34,12 @@ def grf64():
     return n, g, f, ref
 
 
-def test_variable_coefficient_n64_fp64_direct(acr, grf64):
-    """FP64 ACR as a direct solver: within 10x the truncation tolerance."""
+@pytest.mark.parametrize("core_svd", [1, 2])
+def test_variable_coefficient_n64_fp64_direct(acr, grf64, core_svd):
+    """FP64 ACR as a direct solver: within 10x the truncation tolerance, with
+    the Jacobi SVD (1) or the pivoted QR (2) truncating the recompression core."""
     n, g, f, ref = grf64
-    h = acr.acr_factor(n, g, 1e-6, 64)
+    h = acr.acr_factor(n, g, 1e-6, 64, core_svd=core_svd)
     b = to_cols(f)
     x = empty_like_cols(b)
     acr.acr_solve(h, b, x)

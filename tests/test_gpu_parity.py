@@ -79,11 +79,14 @@ def test_intermediate_blocks_match_dense_cr(acr):
     assert rel(acr.acr_get_factor_block(h, 5, 0, 0), Xc) < 1e-11
 
 
+@pytest.mark.parametrize("core_svd", [1, 2])
 @pytest.mark.parametrize("n,leaf,tol", [(16, 32, 1e-8), (16, 16, 1e-6), (32, 32, 1e-6)])
-def test_compressed_fp64_within_ten_tol(acr, n, leaf, tol):
+def test_compressed_fp64_within_ten_tol(acr, n, leaf, tol, core_svd):
+    """FP64 ACR as a direct solver within 10x the truncation tolerance, with
+    either truncation of the recompression core (1: Jacobi SVD, 2: pivoted QR)."""
     g = synthetic.gaussian_random_field(n, 1)
     f = synthetic.uniform_rhs(n, 0)
-    h = acr.acr_factor(n, g, tol, leaf)
+    h = acr.acr_factor(n, g, tol, leaf, core_svd=core_svd)
     u = _solve(acr, h, f)
     ref = direct.dense_solve(n, g, f) if n <= 16 else iterative.reference_solve(n, g, f, rtol=1e-13)
     assert rel(u, ref) < 10 * tol

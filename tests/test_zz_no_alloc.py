@@ -44,6 +44,67 @@ def test_matches_allocating_residual_on_two_calls(acr):
         np.testing.assert_allclose(rel_new, rel_ref, rtol=1e-12)
 
 
+def _pool_bytes():
+    """(reserved, used, used high-water) of the device's default memory pool,
+    which the library's allocating calls draw from, or None without libcudart."""
+    import ctypes as C
+
+    import torch
+
+    rt = None
+    for name in ("libcudart.so.13", "libcudart.so"):
+        try:
+            rt = C.CDLL(name)
+            break
+        except OSError:
+            continue
+    if rt is None:
+        return None
+    pool = C.c_void_p()
+    if rt.cudaDeviceGetDefaultMemPool(C.byref(pool), torch.cuda.current_device()) != 0:
+        return None
+    out = []
+    for attr in (5, 7, 8):  # ReservedMemCurrent, UsedMemCurrent, UsedMemHigh
+        v = C.c_uint64()
+        assert rt.cudaMemPoolGetAttribute(pool, attr, C.byref(v)) == 0
+        out.append(v.value)
+    return out, rt, pool
+
+
+def test_call_allocates_no_device_memory(acr):
+    """After a warm-up call, a call changes neither the free device memory, nor
+    the memory pool the library allocates from (its high-water mark included),
+    nor PyTorch's allocator."""
+    import ctypes as C
+
+    import torch
+
+    n = 16
+    h = acr.acr_factor(n, synthetic.gaussian_random_field(n, 7), 0.0, 32)
+    F = synthetic.multi_rhs(n, range(8))
+    b, x = to_cols(F), to_cols(F[:, ::-1].copy())
+    r = empty_like_cols(b)
+    acr.acr_residual_noalloc(h, b, x, r)  # warm-up: kernels loaded, symbol address looked up
+    torch.cuda.synchronize()
+    pb = _pool_bytes()
+    if pb is not None:
+        (_, used0, _), rt, pool = pb
+        zero = C.c_uint64(0)
+        assert rt.cudaMemPoolSetAttribute(pool, 8, C.byref(zero)) == 0  # high-water mark := current use
+    free0 = torch.cuda.mem_get_info()[0]
+    nalloc0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(3):
+        acr.acr_residual_noalloc(h, b, x, r)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == nalloc0
+    if pb is not None:
+        (res1, used1, high1), _, _ = _pool_bytes()
+        # a reset high-water mark reads as the current use (or 0 until the next
+        # allocation): any allocation during the calls would have raised it above
+        assert used1 == used0 and high1 in (0, used0) and res1 == pb[0][0]
+
+
 def test_rejects_more_rhs_than_its_scratch(acr):
     n = 4
     h = acr.acr_factor(n, None, 0.0, 4)

@@ -80,6 +80,12 @@ typedef struct {
                              beta_z per node, host or device, copied at factor) adding beta . grad u by
                              first-order upwind differences (Section 5, Eq. codi: beta = alpha b(x)); the
                              operator is then non-symmetric and acr_solve_ir_transpose refines with A^T */
+  int chol_passes;        /* ACR_FP32 recompression of blocks wider than 128 rows: passes of the pivoted
+                             Cholesky (0 = default 1, at most 4).  One pass stops where the FP32 Gram matrix
+                             stops resolving (column residuals ~3e-3 of the largest), so tol below that is
+                             met only approximately; each further pass factors the Gram matrix of the
+                             explicitly formed residual (2 passes reach the FP64 factorisation's ranks at
+                             tol 1e-6).  FP32 rounding, not truncation, then bounds the preconditioner */
 } acr_opts;
 
 typedef struct {

@@ -51,6 +51,7 @@ class AcrOpts(C.Structure):
         ("coarse_dense_max", C.c_int),
         ("graphs", C.c_int),
         ("velocity", C.c_void_p),
+        ("chol_passes", C.c_int),
     ]
 
 

@@ -688,6 +688,7 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     c.inverse_fp64 = o.inverse_fp64 != 0;
     c.tensor = o.tensor_cores != 0;
     c.core_svd = o.core_svd;
+    c.chol_passes = o.chol_passes > 0 ? std::min(o.chol_passes, 4) : 1;
     ACR_CUDA(cudaMalloc(&c.d_flag, 4 * sizeof(int)));
     ACR_CUDA(cudaMemsetAsync(c.d_flag, 0, 4 * sizeof(int), c.st));
     ACR_CUDA(cudaMalloc(&c.d_jflops, sizeof(double)));

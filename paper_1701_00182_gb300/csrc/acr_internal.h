@@ -58,6 +58,7 @@ struct Ctx {
   bool inverse_fp64 = false;  // FP32 factorisation: leaf and coupling inverses in FP64
   bool tensor = false;        // FP32 GEMMs of large tiles on the tensor cores (3xTF32)
   int force_cfg = -1;         // ACR_GEMM_CFG=<i>: every GEMM uses tiling i where it is valid (debugging)
+  int chol_passes = 1;         // pivoted-Cholesky passes of the FP32 recompression (1 = Gram floor only)
   int core_svd = 0;           // core truncation: 0 / 2 pivoted QR (default), 1 Jacobi SVD
   void check_range(const void* base, long lo, long hi, size_t es, const char* what) const;
   bool profile = false;  // record CUDA events around every launch, accumulated per kernel class

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "../../include/acr.h"
 #include "acr_internal.h"
 
 namespace acr {
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(256) k_mirror_scale(int r, long NB, T* G, cons
   const long z = blockIdx.x;  // matrix: side = z / NB, block z % NB
   const int nt = (r + 31) / 32;
   T* M = G + z * (long)r * r;
-  const T* a = (z < NB) ? aL + z * r : aR + (z - NB) * r;
+  const T* a = aL ? ((z < NB) ? aL + z * r : aR + (z - NB) * r) : nullptr;  // null: mirror only
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int pr = blockIdx.y; pr < nt * nt; pr += gridDim.y) {
     const int ti = pr / nt, tj = pr % nt;
@@ -173,11 +174,11 @@ __global__ void __launch_bounds__(256) k_mirror_scale(int r, long NB, T* G, cons
       const int i = i0 + ii, j = j0 + tx;
       if (i < r && j < r) {
         const T v = (ti < tj || ii <= tx) ? t[ii][tx] : t[tx][ii];
-        M[(long)i * r + j] = v * a[i] * a[j];
+        M[(long)i * r + j] = a ? v * a[i] * a[j] : v;
       }
       if (ti < tj) {  // mirror tile (tj, ti): row j0 + ii, column i0 + tx
         const int mi = j0 + ii, mj = i0 + tx;
-        if (mi < r && mj < r) M[(long)mi * r + mj] = t[tx][ii] * a[mi] * a[mj];
+        if (mi < r && mj < r) M[(long)mi * r + mj] = a ? t[tx][ii] * a[mi] * a[mj] : t[tx][ii];
       }
     }
     __syncthreads();
@@ -185,13 +186,26 @@ __global__ void __launch_bounds__(256) k_mirror_scale(int r, long NB, T* G, cons
 }
 
 // ---- pivoted Cholesky of a Gram matrix --------------------------------------
-// G (r x r, symmetric PSD) ~ P R^T R P^T; R rows t < kk are valid (original
-// column order, zero in already chosen columns), the rest zero.  Stops when
-// the largest remaining diagonal is <= eps * (largest initial diagonal).
+// G (r x r, symmetric PSD) ~ P R^T R P^T.  Rows t of R are written at row
+// off + t (off = kkall[j] on entry when `resume`, else 0; original column
+// order, zero in already chosen columns), pivots at piv[off + t], and kkall[j]
+// becomes off + (pivots found).  Stops when the largest remaining diagonal is
+// <= max(eps * (largest initial diagonal of this G), eps_abs * dref[j])
+// (dref: the first pass's largest initial diagonal; null = no absolute floor).
+// dmax_out[j] (if given) receives this G's largest initial diagonal.
+//
+// A resumed pass factors the Gram matrix of the explicitly formed residual
+// F1 = F - Q1 R1 of the first pass: its Schur complement is recomputed from
+// data instead of by subtraction in Gram space, which is what limits a single
+// FP32 pass (the FP32 Gram holds entries to ~1e-7 of the largest, so a
+// column whose residual is below ~3e-3 of the largest cannot be resolved).
+// Columns chosen by the first pass have exact zero residual and are never
+// chosen again, so the rows of both passes form one upper-triangular factor
+// in pivot order.
 constexpr int kCholThreads = 1024;
 template <class T>
-__global__ void __launch_bounds__(kCholThreads) k_pchol(int r, const T* Gall, T eps, T* Rall, int* pivall,
-                                                        int* kkall) {
+__global__ void __launch_bounds__(kCholThreads) k_pchol(int r, const T* Gall, T eps, T eps_abs, const T* dref,
+                                                        int resume, T* Rall, int* pivall, int* kkall, T* dmax_out) {
   extern __shared__ unsigned char smraw[];
   T* d = reinterpret_cast<T*>(smraw);
   T* colp = d + r;  // R[0..t)[p] of the current pivot column
@@ -201,13 +215,19 @@ __global__ void __launch_bounds__(kCholThreads) k_pchol(int r, const T* Gall, T 
   __shared__ int s_p;
   const long j = blockIdx.x;
   const T* G = Gall + j * (long)r * r;
-  T* R = Rall + j * (long)r * r;
-  int* piv = pivall + j * r;
+  const int off = resume ? kkall[j] : 0;
+  T* R = Rall + j * (long)r * r + (long)off * r;
+  int* piv = pivall + j * r + off;
+  const T floor_abs = dref ? eps_abs * dref[j] : T(0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int i = tid; i < r; i += blockDim.x) d[i] = fmax(G[(long)i * r + i], T(0));
   __syncthreads();
+  // columns chosen by earlier passes stay out (their rows here are exact zeros)
+  for (int u = tid; u < off; u += blockDim.x) d[piv[u - off]] = T(-1);
+  __syncthreads();
   int t = 0;
-  for (; t < r; ++t) {
+  const int tmax = r - off;
+  for (; t < tmax; ++t) {
     T best = T(-1);
     int bi = 0x7fffffff;
     for (int i = tid; i < r; i += blockDim.x)
@@ -236,7 +256,7 @@ __global__ void __launch_bounds__(kCholThreads) k_pchol(int r, const T* Gall, T 
     __syncthreads();
     const T dp = s_dp;
     const int p = s_p;
-    if (!(dp > eps * s_dmax0) || !(dp > T(0))) break;
+    if (!(dp > eps * s_dmax0) || !(dp > floor_abs) || !(dp > T(0))) break;
     for (int u = tid; u < t; u += blockDim.x) colp[u] = R[(long)u * r + p];
     __syncthreads();
     const T sq = sqrt(dp), isq = T(1) / sq;
@@ -265,8 +285,59 @@ __global__ void __launch_bounds__(kCholThreads) k_pchol(int r, const T* Gall, T 
     if (tid == 0) piv[t] = p;
     __syncthreads();
   }
-  for (long e = (long)t * r + tid; e < (long)r * r; e += blockDim.x) R[e] = T(0);
-  if (tid == 0) kkall[j] = t;
+  for (long e = (long)t * r + tid; e < (long)(r - off) * r; e += blockDim.x) R[e] = T(0);
+  if (tid == 0) {
+    kkall[j] = off + t;
+    if (dmax_out) dmax_out[j] = s_dmax0;
+  }
+}
+
+// ---- residual of the first pass ------------------------------------------------
+// W = R11^{-1} R1 per block (k1 x r, row major, ld r) with R11[u][v] =
+// R[u][piv[v]], so that F1 = F - F[:, piv] W is the part of F outside the
+// span of its pivot columns.  One CTA per (block, chunk of C right-hand-side
+// columns), right-looking back substitution as in the rebuild coefficients.
+template <class T>
+__global__ void __launch_bounds__(256) k_resid_coef(int r, const T* __restrict__ Rall, const int* __restrict__ pivall,
+                                                    const int* __restrict__ kkall, T* __restrict__ Wall, int C) {
+  extern __shared__ unsigned char smraw[];
+  T* B = reinterpret_cast<T*>(smraw);  // k x C
+  const long j = blockIdx.x;
+  const int i0 = blockIdx.y * C;
+  const int tc = threadIdx.x % C, g = threadIdx.x / C, G = blockDim.x / C;
+  const int i = i0 + tc;
+  const int k = kkall[j];
+  const T* R = Rall + j * (long)r * r;
+  const int* piv = pivall + j * r;
+  T* W = Wall + j * (long)r * r;
+  const bool act = i < r;
+  for (int u = g; u < k; u += G) B[u * C + tc] = act ? R[(long)u * r + i] : T(0);
+  __syncthreads();
+  for (int u = k - 1; u >= 0; --u) {
+    const int pu = piv[u];
+    const T zu = B[u * C + tc] / R[(long)u * r + pu];
+    const T* Rc = R + pu;
+#pragma unroll 4
+    for (int w = g; w < u; w += G) B[w * C + tc] -= Rc[(long)w * r] * zu;
+    if (g == 0 && act) W[(long)u * r + i] = zu;
+    __syncthreads();
+  }
+}
+
+// F1 = F diag(a): the balanced copy of one side's factor; row i of cluster c
+// of a plane belongs to block (plane, c ^ side) and uses that block's scales.
+template <class T>
+__global__ void k_scale_cols(int P, int m, int s, int nclus, int r, long NB, int side, const T* F, const T* a,
+                             T* out) {
+  const long nrow = (long)P * m;
+  const int lane = threadIdx.x & 31;
+  for (long rw = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; rw < nrow;
+       rw += ((long)gridDim.x * blockDim.x) >> 5) {
+    const long plane = rw / m;
+    const int i = (int)(rw - plane * m);
+    const T* sc = a + (plane * nclus + ((i / s) ^ side)) * (long)r;
+    for (int u = lane; u < r; u += 32) out[rw * r + u] = F[rw * r + u] * sc[u];
+  }
 }
 
 // ---- one-sided Jacobi SVD of the core ----------------------------------------
@@ -821,15 +892,77 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
         r, NB, G.p, scale.p, scale.p + NB * r);
     c.kend(KC_COPY, 0, 2.0 * NB * sizeof(T) * 1.5 * r * r, "copy:balance");
     c.launches += 1;
-    double epsd = std::max(0.01 * tol * tol, sizeof(T) == 8 ? 1e-15 : 1e-5);
+    // FP32: the Gram matrix resolves a column's residual down to ~3e-3 of the
+    // largest (1e-5 on the squared diagonal); FP64 to ~3e-8.
+    const double floor_rel = sizeof(T) == 8 ? 1e-15 : 1e-5;
+    const double tau = 0.01 * tol * tol;  // squared column residual the tolerance asks for
+    const double epsd = std::max(tau, floor_rel);
     size_t sm = 2 * (size_t)r * sizeof(T);
     if (sm > 48 * 1024) ACR_CUDA(cudaFuncSetAttribute(k_pchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    c.kbegin();
     // one thread per Gram column (64 .. 1024): small blocks at deep levels do
     // not pay for idle warps in every per-pivot barrier
     const int thr = std::min(kCholThreads, std::max(64, (r + 31) / 32 * 32));
-    k_pchol<T><<<(unsigned)(2 * NB), thr, sm, c.st>>>(r, G.p, T(epsd), R.p, piv.p, kk.p);
+    DBuf<T> dmax(c, 2 * NB);
+    c.kbegin();
+    k_pchol<T><<<(unsigned)(2 * NB), thr, sm, c.st>>>(r, G.p, T(epsd), T(0), nullptr, 0, R.p, piv.p, kk.p, dmax.p);
     c.kend(KC_PCHOL, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r);
+    // Further passes while the floor stopped above the tolerance: each factors
+    // the Gram matrix of the explicit residual F1 = F~ - F~[:, piv] R11^{-1} R1
+    // (F~ = F diag(a), the balanced factor) and appends its rows to R.
+    const int passes = tau < epsd ? c.chol_passes : 1;
+    for (int pass = 1; pass < passes; ++pass) {
+      std::vector<int> hk1(2 * NB);
+      ACR_CUDA(cudaMemcpyAsync(hk1.data(), kk.p, 2 * NB * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+      ACR_CUDA(cudaStreamSynchronize(c.st));
+      int k1 = 0;
+      for (int v : hk1) k1 = std::max(k1, v);
+      if (k1 == 0 || k1 >= r) break;
+      DBuf<T> W(c, 2 * NB * (size_t)r * r, true);
+      {
+        int Cw = 32;
+        while (Cw > 8 && (size_t)k1 * Cw * sizeof(T) > 100 * 1024) Cw /= 2;
+        const size_t smw = (size_t)k1 * Cw * sizeof(T);
+        if (smw > 200 * 1024) throw AcrError(ACR_ERR_RANK_CAP, "recompression rank too large for the residual pass");
+        if (smw > 48 * 1024)
+          ACR_CUDA(cudaFuncSetAttribute(k_resid_coef<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+        c.kbegin();
+        k_resid_coef<T><<<dim3((unsigned)(2 * NB), (unsigned)((r + Cw - 1) / Cw)), 256, smw, c.st>>>(
+            r, R.p, piv.p, kk.p, W.p, Cw);
+        double f = 0;
+        for (int v : hk1) f += (double)v * v * r;
+        c.kend(KC_COEF, f, 2.0 * NB * sizeof(T) * 2.0 * r * r, "resid_coef");
+      }
+      DBuf<T> F1(c, (size_t)P * m * r), Gc1(c, (size_t)P * m * k1);
+      for (int side = 0; side < 2; ++side) {
+        const unsigned gblk = (unsigned)std::min<long>(((long)P * m * 32 + 255) / 256, 152L * 32);
+        c.kbegin();
+        k_scale_cols<T><<<gblk, 256, 0, c.st>>>(P, m, s, nclus, r, NB, side, side ? Rb.p : Lb.p,
+                                                scale.p + side * NB * r, F1.p);
+        c.kend(KC_COPY, 0, (double)sizeof(T) * 2.0 * P * m * r, "copy:scale_cols");
+        c.kbegin();
+        k_gather_piv<T><<<gblk, 256, 0, c.st>>>(P, m, s, nclus, r, k1, NB, side, F1.p, piv.p, kk.p, Gc1.p);
+        c.kend(KC_COPY, 0, (double)sizeof(T) * 2.0 * P * m * k1, "copy:gather_piv");
+        // F1 -= F1[:, piv] W  (the block of a row of cluster c is c ^ side)
+        Op<T> A{Gc1.p, k1, 1, (long)m * k1, (long)s * k1, 0, 0, 0};
+        Op<T> B{W.p + side * NB * (long)r * r, r, 1, (long)nclus * r * r, (long)r * r, 0, 0, side};
+        Op<T> Cm{F1.p, r, 1, (long)m * r, (long)s * r, 0, 0, 0};
+        c.tag = "resid";
+        gemm<T>(c, s, r, k1, P, nclus, T(-1), A, B, T(1), Cm);
+        Op<T> GA{F1.p, 1, r, (long)m * r, (long)s * r, 0, 0, side};
+        Op<T> GB{F1.p, r, 1, (long)m * r, (long)s * r, 0, 0, side};
+        Op<T> GC{G.p + side * NB * r * (long)r, r, 1, (long)nclus * r * r, (long)r * r, 0, 0, 0};
+        c.tag = "gram2";
+        gemm_sym<T>(c, r, s, P, nclus, T(1), GA, GB, T(0), GC, false);
+      }
+      c.kbegin();
+      k_mirror_scale<T><<<dim3((unsigned)(2 * NB), (unsigned)std::min(nt * nt, 65535)), 256, 0, c.st>>>(
+          r, NB, G.p, nullptr, nullptr);
+      c.kend(KC_COPY, 0, 2.0 * NB * sizeof(T) * 1.5 * r * r, "copy:mirror");
+      c.kbegin();
+      k_pchol<T><<<(unsigned)(2 * NB), thr, sm, c.st>>>(r, G.p, T(floor_rel), T(tau), dmax.p, 1, R.p, piv.p,
+                                                        kk.p, nullptr);
+      c.kend(KC_PCHOL, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r);
+    }
   }
   // Ranks of the two factorisations: the core only needs its leading
   // kL x kR block (the truncation kernels read nothing else).

@@ -67,23 +67,59 @@ def test_variable_coefficient_n64_fp32_refined(acr, grf64, tensor_cores):
             assert k <= (m >> (lvl + 1)) // 2, (lvl, k, row)
 
 
-def test_helmholtz_n64_fgmres_ranks(acr):
+@pytest.mark.parametrize("precision,restart", [("fp32", 200), ("fp64", 50)])
+def test_helmholtz_n64_fgmres_ranks(acr, precision, restart):
     """Indefinite Helmholtz, 10 points per wavelength: ACR at tol 1e-4 as the
-    right preconditioner of FP64 FGMRES(50) to 1e-10.  The factorisation runs
-    in FP64: in FP32 this operator's reduced blocks lose all accuracy at
-    n = 64 (measured one-solve residuals of 5e2 - 3e5 and a stalled FGMRES)."""
+    right preconditioner of FP64 FGMRES to 1e-10 (oracle residual), with the
+    ranks reported per CR level and HODLR level.  The FP32 factorisation is a
+    usable preconditioner of this operator only when its recompression
+    resolves the tolerance (two pivoted-Cholesky passes; with one pass,
+    FGMRES stalls near 1) and with a long restart (the preconditioned spectrum
+    has many outliers: FGMRES(50) stalls near 0.33, FGMRES(200) converges in
+    ~100 applications); FP64 converges with 50."""
     n = 64
     w = synthetic.helmholtz_omega(n)
     f = synthetic.point_source(n, 3)
-    h = acr.acr_factor(n, None, 1e-4, 64, precision=acr.ACR_FP64, shift=-w * w)
+    prec = acr.ACR_FP32 if precision == "fp32" else acr.ACR_FP64
+    h = acr.acr_factor(n, None, 1e-4, 64, precision=prec, shift=-w * w, tensor_cores=1, chol_passes=2)
     b = to_cols(f)
     x = empty_like_cols(b)
-    it, relr, _ = acr.acr_solve_fgmres(h, b, x, rtol=1e-10, restart=50, maxit=400)
+    it, relr, _ = acr.acr_solve_fgmres(h, b, x, rtol=1e-10, restart=restart, maxit=400)
     u = from_cols(x)[:, 0]
     assert iterative.rel_residual(n, None, u, f, shift=-w * w)[0] <= 1.01e-10
     s = acr.acr_get_stats(h)
     assert len(s["max_rank"]) == s["levels_cr"] + 1
     assert all(len(row) == s["levels_h"] for row in s["max_rank"])
+    # the level-0 operator's exact cut ranks, then compressed ranks below the block size
+    assert s["max_rank_d"][0] == [64, 32, 32, 16, 16, 8]
+    for row in s["max_rank_d"][1:]:
+        for lvl, k in enumerate(row):
+            assert 0 < k <= (n * n >> (lvl + 1)) // 2, (lvl, row)
+    print("helmholtz %s: %d FGMRES(%d) applications; max rank per CR level %s"
+          % (precision, it, restart, [max(r) for r in s["max_rank_d"]]))
+
+
+def test_fp32_residual_pass_reaches_fp64_ranks(acr, grf64):
+    """A second pivoted-Cholesky pass on the explicitly formed residual lets the
+    FP32 recompression resolve the tolerance: its block ranks rise from the
+    FP32 Gram floor's to within 10 % of the FP64 factorisation's, and the
+    refined solve still converges."""
+    n, g, f, ref = grf64
+    ranks = {}
+    for key, kw in (("f32x1", dict(precision=acr.ACR_FP32, chol_passes=1)),
+                    ("f32x2", dict(precision=acr.ACR_FP32, chol_passes=2)),
+                    ("f64", dict(precision=acr.ACR_FP64))):
+        h = acr.acr_factor(n, g, 1e-6, 64, tensor_cores=1, **kw)
+        s = acr.acr_get_stats(h)
+        ranks[key] = max(max(r) for r in s["max_rank_d"])
+        if key == "f32x2":
+            b = to_cols(f)
+            x = empty_like_cols(b)
+            it, relr, _ = acr.acr_solve_ir(h, b, x, rtol=1e-10, maxit=40)
+            assert iterative.rel_residual(n, g, from_cols(x)[:, 0], f)[0] <= 1.01e-10
+        h.close()
+    assert ranks["f32x2"] > ranks["f32x1"]
+    assert abs(ranks["f32x2"] - ranks["f64"]) <= 0.1 * ranks["f64"], ranks
 
 
 def test_full_size_multi_rhs_sampled(acr):

@@ -59,6 +59,7 @@ struct Ctx {
   bool tensor = false;        // FP32 GEMMs of large tiles on the tensor cores (3xTF32)
   int force_cfg = -1;         // ACR_GEMM_CFG=<i>: every GEMM uses tiling i where it is valid (debugging)
   int chol_passes = 1;         // pivoted-Cholesky passes of the FP32 recompression (1 = Gram floor only)
+  bool qrcp_cluster = true;    // pivoted QR of large cores / explicit blocks on a thread-block cluster
   int core_svd = 0;           // core truncation: 0 / 2 pivoted QR (default), 1 Jacobi SVD
   void check_range(const void* base, long lo, long hi, size_t es, const char* what) const;
   bool profile = false;  // record CUDA events around every launch, accumulated per kernel class
@@ -231,6 +232,17 @@ void col_scale_copy(Ctx& c, long N, int nrhs, const double* a, const double* x, 
 // ---- dense coarsest plane (coarse.cu) ---------------------------------------
 void dense_inverse_fp64(Ctx& c, int m, double* A, double* Xinv);
 template <class S, class D> void convert(Ctx& c, long n, const S* a, D* b);
+
+// ---- cluster pivoted QR (qrcp_cluster.cu) -----------------------------------
+// Truncation of NB matrices C_bi (valid kk[bi] x kk[NB + bi], row major, ld r)
+// by a column-pivoted QR held in the distributed shared memory of a cluster
+// of up to 8 CTAs: C ~ X diag(sig) Y^T, ranks in rank (the form of the one-CTA
+// kernel).  frob: stop criterion on the remaining columns' Frobenius norm;
+// floor2 (per block, or null): squared column norm that is never chosen.
+// Returns false (nothing launched) when the matrices do not fit.
+template <class T>
+bool qrcp_cluster(Ctx& c, int r, const T* C, const int* kk, long NB, int kmaxL, int kmaxR, double tol, int frob,
+                  const T* floor2, T* X, T* Y, T* sig, int* rank, const char* site);
 
 // ---- recompression (recompress.cu) ----------------------------------------
 // Level-l recompression of the off-diagonal blocks  Left|c * Right|c^1 ^T  for

@@ -576,17 +576,23 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(int r, const T* Call, co
 // norm).  Output in the same form as the Jacobi SVD: C ~ X diag(sig) Y^T with
 // X = Q_k (kL x k, orthonormal), sig_t = |R_tt|, Y[Pi(j)][t] = R[t][j] / sig_t.
 constexpr int kQrcpThreads = 1024;
+// frob = 1: stop instead when the remaining columns' squared norms sum to
+// <= tol^2 * (largest initial), which bounds the truncation error of the whole
+// block by tol * sigma_1 however many columns remain (explicit blocks).
+// floor2 (per block, or null): squared column norm below which a column is
+// rounding noise of the block's formation and is never chosen.
 template <class T>
 __global__ void __launch_bounds__(kQrcpThreads) k_qrcp(int r, const T* Call, const int* kk, long NB, T* Wall,
                                                        T* Xall, T* Yall, T* sigall, int* rankall, T tol,
-                                                       int smem_elems, double* flops_out) {
+                                                       int smem_elems, double* flops_out, int frob,
+                                                       const T* floor2) {
   extern __shared__ unsigned char smraw[];
   T* nrm = reinterpret_cast<T*>(smraw);
   T* nrm0 = nrm + r;
   T* tau = nrm0 + r;
   int* perm = reinterpret_cast<int*>(tau + r);
   T* Ws = reinterpret_cast<T*>(perm + r + (r & 1));
-  __shared__ T wv[32];
+  __shared__ T wv[32], ws[32];
   __shared__ int wi[32];
   __shared__ T s_thr2;
   __shared__ int s_p, s_stop;
@@ -620,25 +626,30 @@ __global__ void __launch_bounds__(kQrcpThreads) k_qrcp(int r, const T* Call, con
   int rank = 0;
   for (int st = 0; st < kmax; ++st) {
     // pivot: largest remaining column norm
-    T best = T(-1);
+    T best = T(-1), sum = T(0);
     int bi2 = 0x7fffffff;
-    for (int j = st + tid; j < kR; j += blockDim.x)
+    for (int j = st + tid; j < kR; j += blockDim.x) {
+      sum += fmax(nrm[j], T(0));
       if (nrm[j] > best) { best = nrm[j]; bi2 = j; }
+    }
     for (int o = 16; o > 0; o >>= 1) {
       T ov = __shfl_xor_sync(0xffffffffu, best, o);
       int oi = __shfl_xor_sync(0xffffffffu, bi2, o);
+      sum += __shfl_xor_sync(0xffffffffu, sum, o);
       if (ov > best || (ov == best && oi < bi2)) { best = ov; bi2 = oi; }
     }
-    if (lane == 0) { wv[warp] = best; wi[warp] = bi2; }
+    if (lane == 0) { wv[warp] = best; wi[warp] = bi2; ws[warp] = sum; }
     __syncthreads();
     if (tid == 0) {
-      T b = T(-1);
+      T b = T(-1), sm = T(0);
       int bb = st;
-      for (int w = 0; w < nw; ++w)
+      for (int w = 0; w < nw; ++w) {
+        sm += ws[w];
         if (wv[w] > b || (wv[w] == b && wi[w] < bb)) { b = wv[w]; bb = wi[w]; }
+      }
       if (st == 0) s_thr2 = tol * tol * b;
       s_p = bb;
-      s_stop = !(b > s_thr2) || !(b > T(0));
+      s_stop = !((frob ? sm : b) > s_thr2) || !(b > (floor2 ? floor2[bi] : T(0)));
     }
     __syncthreads();
     if (s_stop) break;
@@ -830,10 +841,135 @@ __global__ void k_gather_piv(int P, int m, int s, int nclus, int r, int kmax, lo
   }
 }
 
+// Squared column norms of a factor over each cluster: out[(plane nclus + c)
+// r + k] = sum over the rows i of cluster c of F[plane][i][k]^2.  CTA: 32
+// columns x 8 row groups (rows coalesced 128 bytes at a time).
+template <class T>
+__global__ void __launch_bounds__(256) k_cluster_colnorm2(int m, int s, int nclus, int r, const T* F, float* out) {
+  __shared__ float part[8][33];
+  const long bc = blockIdx.x;  // plane * nclus + cluster
+  const long plane = bc / nclus;
+  const int c = (int)(bc % nclus);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int k = blockIdx.y * 32 + tx;
+  const T* Fc = F + (plane * m + (long)c * s) * r;
+  float a = 0.f;
+  if (k < r)
+    for (int i = ty; i < s; i += 8) {
+      const float v = (float)Fc[(long)i * r + k];
+      a += v * v;
+    }
+  part[ty][tx] = a;
+  __syncthreads();
+  if (ty == 0 && k < r) {
+    float t = 0.f;
+    for (int g = 0; g < 8; ++g) t += part[g][tx];
+    out[bc * r + k] = t;
+  }
+}
+
+// Rounding-noise floor of an explicit block M_c = L|c R|c^1^T formed by one
+// GEMM: its error is ~ u sqrt(r) (sum_k |L_k|^2 |R_k|^2)^(1/2) in Frobenius
+// norm, spread over s columns; floor2 = (4 x that / sqrt(s))^2 keeps every
+// noise column below the stop of the pivoted QR.  One warp per block.
+template <class T>
+__global__ void k_explicit_floor(long NB, int s, int r, const float* nL, const float* nR, double u, T* floor2) {
+  const long bi = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (bi >= NB) return;
+  double acc = 0;
+  for (int k = lane; k < r; k += 32) acc += (double)nL[bi * r + k] * nR[(bi ^ 1) * r + k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) floor2[bi] = T(16.0 * u * u * r * acc / s);
+}
+
+// Factors of blocks truncated in explicit form: block bi = (plane, cluster c)
+// was given as C_bi = M_c^T ~ X diag(sig) Y^T, so M_c ~ (Y S^1/2)(X S^1/2)^T:
+// U|c = Y sqrt(sig), V|c^1 = X sqrt(sig) (columns beyond the block's rank zero).
+// One warp per output row of both panels.
+template <class T>
+__global__ void k_dense_uv(int P, int m, int s, int nclus, int r, int Kout, const T* __restrict__ Xall,
+                           const T* __restrict__ Yall, const T* __restrict__ sigall, const int* __restrict__ rankall,
+                           T* __restrict__ U, T* __restrict__ V) {
+  const long nrow = (long)P * m;
+  const int lane = threadIdx.x & 31;
+  for (long rw = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; rw < nrow;
+       rw += ((long)gridDim.x * blockDim.x) >> 5) {
+    const long plane = rw / m;
+    const int i = (int)(rw - plane * m);
+    const int cl = i / s, ii = i - cl * s;
+    const long bu = plane * nclus + cl, bv = plane * nclus + (cl ^ 1);
+    const int ku = rankall[bu], kv = rankall[bv];
+    for (int t = lane; t < Kout; t += 32) {
+      U[rw * Kout + t] = t < ku ? Yall[(bu * r + ii) * (long)r + t] * sqrt(sigall[bu * r + t]) : T(0);
+      V[rw * Kout + t] = t < kv ? Xall[(bv * r + ii) * (long)r + t] * sqrt(sigall[bv * r + t]) : T(0);
+    }
+  }
+}
+
+// Truncation of NB cores C_bi (valid kk[bi] x kk[NB + bi], row major, ld r):
+// C ~ X diag(sig) Y^T with the ranks in `rank` (pivoted QR by default, or the
+// one-sided Jacobi SVD).
+template <class T>
+static void truncate_cores(Ctx& c, int r, const T* C, const int* kk, long NB, int kmaxL, int kmaxR, double tol,
+                           DBuf<T>& Xo, DBuf<T>& Yo, DBuf<T>& sig, DBuf<int>& rank, const char* site, int frob,
+                           const T* floor2 = nullptr) {
+  DBuf<T> W(c, NB * (size_t)r * r);
+  Xo = DBuf<T>(c, NB * (size_t)r * r);
+  Yo = DBuf<T>(c, NB * (size_t)r * r);
+  sig = DBuf<T>(c, NB * (size_t)r);
+  rank = DBuf<int>(c, NB);
+  const size_t cap = 200 * 1024;
+  if (c.core_svd != 1) {
+    size_t base2 = (size_t)r * (3 * sizeof(T) + sizeof(int)) + ((r & 1) ? sizeof(int) : 0);
+    base2 = (base2 + 15) / 16 * 16;
+    int se2 = (int)std::min<size_t>((size_t)r * r, cap > base2 ? (cap - base2) / sizeof(T) : 0);
+    size_t sm2 = base2 + (size_t)se2 * sizeof(T);
+    // Matrices beyond one CTA's shared memory: the cluster kernel keeps them on chip.
+    if ((long)kmaxL * kmaxR > se2 && c.qrcp_cluster &&
+        qrcp_cluster<T>(c, r, C, kk, NB, kmaxL, kmaxR, tol, frob, floor2, Xo.p, Yo.p, sig.p, rank.p, site))
+      return;
+    ACR_CUDA(cudaFuncSetAttribute(k_qrcp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    c.kbegin();
+    const int thr = std::min(kQrcpThreads, std::max(64, (8 * std::max(kmaxL, kmaxR) + 31) / 32 * 32));
+    k_qrcp<T><<<(unsigned)NB, thr, sm2, c.st>>>(r, C, kk, NB, W.p, Xo.p, Yo.p, sig.p, rank.p, T(tol), se2,
+                                                c.d_jflops, frob, floor2);
+    c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r, site);
+  } else {
+    DBuf<T> Vw(c, NB * (size_t)r * r);
+    size_t base = (size_t)r * (sizeof(T) + sizeof(int)) + ((r & 1) ? sizeof(int) : 0);
+    base = (base + 15) / 16 * 16;
+    int smem_elems = (int)std::min<size_t>((size_t)r * r, cap > base ? (cap - base) / sizeof(T) : 0);
+    size_t sm = base + (size_t)smem_elems * sizeof(T);
+    ACR_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    c.kbegin();
+    k_jacobi<T><<<(unsigned)NB, kJacThreads, sm, c.st>>>(r, C, kk, NB, W.p, Vw.p, Xo.p, Yo.p, sig.p, rank.p, T(tol),
+                                                         24, smem_elems, c.d_flag + 1, c.d_jflops);
+    c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r, site);
+  }
+}
+
+// A block is truncated in explicit form (one GEMM forms it, one pivoted QR
+// truncates it) when its concatenated width reaches its size and it is at
+// most 512 rows (its pivoted QR then runs out of a cluster's shared memory);
+// it is then also more accurate than the Gram route in FP32 (Householder
+// instead of a squared condition number).
+static bool explicit_block(int s, int r) { return s <= 512 && r >= s; }
+
+// Per-site profile label of a recompression launch: kernel, block size s and
+// whether the block was made explicit first.
+static const char* site_name(Ctx& c, const char* kern, int s, bool dens) {
+  if (!c.site_detail) return kern;
+  char buf[96];
+  std::snprintf(buf, sizeof(buf), "%s s=%d%s", kern, s, dens ? " dense" : "");
+  return c.tagstore.insert(buf).first->c_str();
+}
+
 template <class T>
 void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& Right, int r, double tol, bool exact,
                       DBuf<T>& Uout, DBuf<T>& Vout, int& Kout) {
   const int s = m >> (lvl + 1);
+  bool dens = false;
   const int nclus = 1 << (lvl + 1);
   const long NB = (long)P * nclus;
   DBuf<T> Lb = std::move(Left), Rb = std::move(Right);
@@ -843,8 +979,62 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     Vout.release();
     return;
   }
+  if (!exact && explicit_block(s, r)) {
+    // Explicit form: M_c^T = R|c^1 (L|c)^T (s x s) for every block (plane, c),
+    // stored at cluster c; its pivoted QR truncated at tol gives the factors.
+    DBuf<T> Mt(c, (size_t)P * m * s);
+    {
+      Op<T> A{Rb.p, r, 1, (long)m * r, (long)s * r, 0, 0, 1};
+      Op<T> B{Lb.p, 1, r, (long)m * r, (long)s * r, 0, 0, 0};
+      Op<T> C{Mt.p, s, 1, (long)m * s, (long)s * s, 0, 0, 0};
+      c.tag = "explicit";
+      gemm<T>(c, s, s, r, P, nclus, T(1), A, B, T(0), C);
+    }
+    DBuf<T> fl2(c, NB);
+    {
+      // 3xTF32 tensor-core products carry ~2^-22 relative error per product
+      const double u = sizeof(T) == 8 ? 1.1e-16 : (c.tensor ? 2.4e-7 : 6e-8);
+      DBuf<float> nrm(c, 2 * NB * (size_t)r);
+      c.kbegin();
+      const dim3 g((unsigned)NB, (unsigned)((r + 31) / 32));
+      k_cluster_colnorm2<T><<<g, 256, 0, c.st>>>(m, s, nclus, r, Lb.p, nrm.p);
+      k_cluster_colnorm2<T><<<g, 256, 0, c.st>>>(m, s, nclus, r, Rb.p, nrm.p + NB * r);
+      k_explicit_floor<T><<<(unsigned)((NB * 32 + 255) / 256), 256, 0, c.st>>>(NB, s, r, nrm.p, nrm.p + NB * r, u,
+                                                                            fl2.p);
+      c.kend(KC_COPY, 0, (double)sizeof(T) * 2.0 * P * m * r, site_name(c, "copy:explicit_floor", s, true));
+      c.launches += 2;
+    }
+    Lb.release();
+    Rb.release();
+    DBuf<int> kk(c, 2 * NB);
+    fill<int>(c, kk.p, 2 * NB, s);
+    DBuf<T> Xo, Yo, sig;
+    DBuf<int> rank;
+    // FP64: stop on the remaining columns' Frobenius norm (block error <= tol
+    // sigma_1).  FP32: on the largest remaining column -- the Frobenius sum of
+    // s rounding-level columns (~u sqrt(s) each) exceeds tol^2 at tol ~1e-6.
+    truncate_cores<T>(c, s, Mt.p, kk.p, NB, s, s, tol, Xo, Yo, sig, rank, site_name(c, "qrcp", s, true),
+                      sizeof(T) == 8 ? 1 : 0, fl2.p);
+    std::vector<int> hr(NB);
+    ACR_CUDA(cudaMemcpyAsync(hr.data(), rank.p, NB * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    ACR_CUDA(cudaStreamSynchronize(c.st));
+    Kout = 0;
+    for (int v : hr) Kout = std::max(Kout, v);
+    if (Kout == 0) {
+      Uout.release();
+      Vout.release();
+      return;
+    }
+    Uout = DBuf<T>(c, (size_t)P * m * Kout);
+    Vout = DBuf<T>(c, (size_t)P * m * Kout);
+    c.kbegin();
+    k_dense_uv<T><<<(unsigned)std::min<long>(((long)P * m * 32 + 255) / 256, 152L * 32), 256, 0, c.st>>>(
+        P, m, s, nclus, s, Kout, Xo.p, Yo.p, sig.p, rank.p, Uout.p, Vout.p);
+    c.kend(KC_COPY, 0, (double)sizeof(T) * 2.0 * P * m * (s + Kout), site_name(c, "copy:dense_uv", s, true));
+    return;
+  }
   if (r > s) {
-    // Explicit block: U|c = I_s, V|c^1 = R|c^1 (L|c)^T.
+    // Explicit block kept exact: U|c = I_s, V|c^1 = R|c^1 (L|c)^T.
     DBuf<T> U2(c, (size_t)P * m * s), V2(c, (size_t)P * m * s);
     set_identity_clusters<T>(c, P, m, s, U2.p, s, (long)m * s);
     Op<T> A{Rb.p, r, 1, (long)m * r, (long)s * r, 0, 0, 1};
@@ -855,6 +1045,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     Lb = std::move(U2);
     Rb = std::move(V2);
     r = s;
+    dens = true;
   }
   if (exact) {
     Uout = std::move(Lb);
@@ -872,7 +1063,8 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     c.kbegin();
     k_qr_small<T><<<(unsigned)(2 * NB), 256, sm, c.st>>>(s, r, nclus, NB, (long)m * r, Lb.p, Rb.p, R.p, piv.p,
                                                          kk.p);
-    c.kend(KC_QR, 2.0 * NB * 4.0 * s * (double)r * r, 2.0 * NB * sizeof(T) * (2.0 * s * r + (double)r * r));
+    c.kend(KC_QR, 2.0 * NB * 4.0 * s * (double)r * r, 2.0 * NB * sizeof(T) * (2.0 * s * r + (double)r * r),
+           site_name(c, "qr_small", s, dens));
   } else {
     DBuf<T> G(c, 2 * NB * r * (size_t)r);
     for (int side = 0; side < 2; ++side) {
@@ -890,7 +1082,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     const int nt = (r + 31) / 32;
     k_mirror_scale<T><<<dim3((unsigned)(2 * NB), (unsigned)std::min(nt * nt, 65535)), 256, 0, c.st>>>(
         r, NB, G.p, scale.p, scale.p + NB * r);
-    c.kend(KC_COPY, 0, 2.0 * NB * sizeof(T) * 1.5 * r * r, "copy:balance");
+    c.kend(KC_COPY, 0, 2.0 * NB * sizeof(T) * 1.5 * r * r, site_name(c, "copy:balance", s, dens));
     c.launches += 1;
     // FP32: the Gram matrix resolves a column's residual down to ~3e-3 of the
     // largest (1e-5 on the squared diagonal); FP64 to ~3e-8.
@@ -905,7 +1097,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     DBuf<T> dmax(c, 2 * NB);
     c.kbegin();
     k_pchol<T><<<(unsigned)(2 * NB), thr, sm, c.st>>>(r, G.p, T(epsd), T(0), nullptr, 0, R.p, piv.p, kk.p, dmax.p);
-    c.kend(KC_PCHOL, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r);
+    c.kend(KC_PCHOL, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r, site_name(c, "pchol", s, dens));
     // Further passes while the floor stopped above the tolerance: each factors
     // the Gram matrix of the explicit residual F1 = F~ - F~[:, piv] R11^{-1} R1
     // (F~ = F diag(a), the balanced factor) and appends its rows to R.
@@ -961,7 +1153,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
       c.kbegin();
       k_pchol<T><<<(unsigned)(2 * NB), thr, sm, c.st>>>(r, G.p, T(floor_rel), T(tau), dmax.p, 1, R.p, piv.p,
                                                         kk.p, nullptr);
-      c.kend(KC_PCHOL, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r);
+      c.kend(KC_PCHOL, 0, 2.0 * NB * sizeof(T) * 2.0 * r * r, site_name(c, "pchol2", s, dens));
     }
   }
   // Ranks of the two factorisations: the core only needs its leading
@@ -987,35 +1179,9 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     c.tag = "core";
     gemm<T>(c, kmaxL, kmaxR, r, 1, (int)NB, T(1), A, B, T(0), C);
   }
-  DBuf<T> W(c, NB * (size_t)r * r), Vw(c, NB * (size_t)r * r), Xo(c, NB * (size_t)r * r),
-      Yo(c, NB * (size_t)r * r), sig(c, NB * (size_t)r);
-  DBuf<int> rank(c, NB);
-  {
-    size_t base = (size_t)r * (sizeof(T) + sizeof(int)) + ((r & 1) ? sizeof(int) : 0);
-    base = (base + 15) / 16 * 16;
-    const size_t cap = 200 * 1024;
-    int smem_elems = (int)std::min<size_t>((size_t)r * r, cap > base ? (cap - base) / sizeof(T) : 0);
-    size_t sm = base + (size_t)smem_elems * sizeof(T);
-    ACR_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    const bool use_qrcp = c.core_svd != 1;
-    if (use_qrcp) {
-      size_t base2 = (size_t)r * (3 * sizeof(T) + sizeof(int)) + ((r & 1) ? sizeof(int) : 0);
-      base2 = (base2 + 15) / 16 * 16;
-      int se2 = (int)std::min<size_t>((size_t)r * r, cap > base2 ? (cap - base2) / sizeof(T) : 0);
-      size_t sm2 = base2 + (size_t)se2 * sizeof(T);
-      ACR_CUDA(cudaFuncSetAttribute(k_qrcp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-      c.kbegin();
-      const int thr = std::min(kQrcpThreads, std::max(64, (8 * std::max(kmaxL, kmaxR) + 31) / 32 * 32));
-      k_qrcp<T><<<(unsigned)NB, thr, sm2, c.st>>>(r, Cc.p, kk.p, NB, W.p, Xo.p, Yo.p, sig.p, rank.p, T(tol),
-                                                           se2, c.d_jflops);
-      c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r);
-    } else {
-      c.kbegin();
-      k_jacobi<T><<<(unsigned)NB, kJacThreads, sm, c.st>>>(r, Cc.p, kk.p, NB, W.p, Vw.p, Xo.p, Yo.p, sig.p, rank.p,
-                                                           T(tol), 24, smem_elems, c.d_flag + 1, c.d_jflops);
-      c.kend(KC_JACOBI, 0, (double)NB * sizeof(T) * 3.0 * r * r);
-    }
-  }
+  DBuf<T> Xo, Yo, sig;
+  DBuf<int> rank;
+  truncate_cores<T>(c, r, Cc.p, kk.p, NB, kmaxL, kmaxR, tol, Xo, Yo, sig, rank, site_name(c, "qrcp", s, dens), 0);
   std::vector<int> hr(NB);
   ACR_CUDA(cudaMemcpyAsync(hr.data(), rank.p, NB * sizeof(int), cudaMemcpyDeviceToHost, c.st));
   ACR_CUDA(cudaStreamSynchronize(c.st));
@@ -1058,7 +1224,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     double f = 0;
     if (!qr)
       for (long i = 0; i < 2 * NB; ++i) f += (double)hk[i] * hk[i] * hr[i % NB];
-    c.kend(KC_COEF, f, 2.0 * NB * sizeof(T) * ((double)r * r + (double)r * Kout));
+    c.kend(KC_COEF, f, 2.0 * NB * sizeof(T) * ((double)r * r + (double)r * Kout), site_name(c, "coef", s, dens));
   }
   Uout = DBuf<T>(c, (size_t)P * m * Kout);
   Vout = DBuf<T>(c, (size_t)P * m * Kout);
@@ -1071,7 +1237,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
       c.kbegin();
       k_gather_piv<T><<<(unsigned)std::min<long>(((long)P * m * 32 + 255) / 256, 152L * 32), 256, 0, c.st>>>(
           P, m, s, nclus, r, kmax, NB, side, F, piv.p, kk.p, Gc.p);
-      c.kend(KC_COPY, 0, (double)sizeof(T) * 2.0 * P * m * kmax, "copy:gather_piv");
+      c.kend(KC_COPY, 0, (double)sizeof(T) * 2.0 * P * m * kmax, site_name(c, "copy:gather_piv", s, dens));
       A = Op<T>{Gc.p, kmax, 1, (long)m * kmax, (long)s * kmax, 0, 0, 0};
     }
     Op<T> B{Z.p + side * NB * r * (long)Kout, Kout, 1, (long)nclus * r * Kout, (long)r * Kout, 0, 0, side};

@@ -708,6 +708,7 @@ void exp_inplace(Ctx& c, double* p, long n) {
   template void expand_leaves<T>(Ctx&, int, int, const T*, T*);
 INST(float)
 INST(double)
+template void fill<int>(Ctx&, int*, long, int);
 #undef INST
 
 }  // namespace acr

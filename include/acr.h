@@ -45,7 +45,7 @@ extern "C" {
 enum {
   ACR_OK = 0,
   ACR_ERR_ARG = 1,           /* invalid argument (sizes, NULL, unsupported n/leaf) */
-  ACR_ERR_OOM = 2,           /* device allocation failed or the memory budget was exceeded */
+  ACR_ERR_OOM = 2,           /* a device allocation failed */
   ACR_ERR_BREAKDOWN = 3,     /* a leaf or coupling pivot was (numerically) zero */
   ACR_ERR_RANK_CAP = 4,      /* a block rank exceeded opts->max_rank */
   ACR_ERR_CUDA = 5,          /* a CUDA runtime call failed (no device, launch failure) */
@@ -61,7 +61,11 @@ typedef struct {
   int precision;          /* ACR_FP64 (default) or ACR_FP32 */
   double shift;           /* diagonal term: -omega^2 for Helmholtz, 0 otherwise */
   int max_rank;           /* 0 = unlimited; else a block rank above it fails with ACR_ERR_RANK_CAP */
-  size_t mem_budget;      /* 0 = unlimited; else bytes the factor store may hold */
+  size_t mem_budget;      /* 0 = unlimited; else bytes the stored factors may hold: the CR levels are kept
+                             while they fit; from the first level that does not, only a checkpoint of that
+                             level's inputs is kept (nothing when it is level 0, which re-assembles from
+                             kappa), and every solve call recomputes those levels and the coarsest plane,
+                             uses them and frees them (see levels_stored, tail_recomputes) */
   int autotune;           /* 1 = time candidate GEMM tilings per shape class and keep the fastest */
   int nrhs_max;           /* solve workspace is sized for this many right-hand sides (default 64) */
   void* cuda_stream;      /* cudaStream_t to run on; NULL = legacy default stream */
@@ -113,6 +117,8 @@ typedef struct {
   int jacobi_sweeps_max;                  /* most Jacobi sweeps any core SVD of the factorisation needed */
   int graphs_captured;                    /* solve graphs captured so far */
   int coarse_dense;                       /* 1 if the coarsest plane has a dense FP64 inverse */
+  int levels_stored;                      /* CR levels whose factors are kept (levels_cr without a memory budget) */
+  long long tail_recomputes;              /* solve calls that recomputed the levels not kept */
 } acr_stats;
 
 /* Default options (FP64, shift 0, unlimited ranks and memory, autotune off, nrhs_max 64). */

@@ -78,6 +78,8 @@ class AcrStats(C.Structure):
         ("jacobi_sweeps_max", C.c_int),
         ("graphs_captured", C.c_int),
         ("coarse_dense", C.c_int),
+        ("levels_stored", C.c_int),
+        ("tail_recomputes", C.c_longlong),
     ]
 
 
@@ -341,6 +343,8 @@ def acr_get_stats(h: Handle) -> dict:
         "jacobi_sweeps_max": s.jacobi_sweeps_max,
         "graphs_captured": s.graphs_captured,
         "coarse_dense": s.coarse_dense,
+        "levels_stored": s.levels_stored,
+        "tail_recomputes": s.tail_recomputes,
         "kernels": {nm: {"ms": s.kc_ms[i], "flops": s.kc_flops[i], "bytes": s.kc_bytes[i],
                          "launches": s.kc_launches[i]} for i, nm in enumerate(KERNEL_CLASSES)},
     }
@@ -380,13 +384,15 @@ def _autograd_function():
         forward: acr_factor + acr_solve (or refinement to rtol); backward:
         lambda = A^{-T} grad_u (acr_solve_transpose, or transpose refinement),
         grad_f = lambda, grad_log_kappa = acr_grad_logkappa(u, lambda).  The
-        factorisation of the forward pass is kept for the backward pass.
+        factorisation of the forward pass is kept for the backward pass; with
+        mem_budget > 0 it keeps only the CR levels that fit in that many bytes,
+        and the forward and backward solves recompute the others.
         """
 
         @staticmethod
-        def forward(ctx, log_kappa, f, n, tol, leaf, precision, rtol):
+        def forward(ctx, log_kappa, f, n, tol, leaf, precision, rtol, mem_budget):
             h = acr_factor(n, log_kappa.detach().contiguous(), tol, leaf, precision=precision,
-                           nrhs_max=1 if f.dim() == 1 else f.shape[1])
+                           nrhs_max=1 if f.dim() == 1 else f.shape[1], mem_budget=int(mem_budget or 0))
             fb = _colmajor(f.detach())
             x = _colmajor(torch.zeros_like(fb))
             if rtol:
@@ -409,7 +415,7 @@ def _autograd_function():
                 acr_solve_transpose(h, g, lam)
             grad = torch.zeros(ctx.n ** 3, dtype=torch.float64, device=u.device)
             acr_grad_logkappa(h, u, lam, grad)
-            return grad, lam, None, None, None, None, None
+            return grad, lam, None, None, None, None, None, None
 
     return ACRSolve
 
@@ -417,9 +423,10 @@ def _autograd_function():
 _ACRSolve = None
 
 
-def acr_solve_autograd(log_kappa, f, n: int, tol: float, leaf: int, precision: int = ACR_FP64, rtol=None):
+def acr_solve_autograd(log_kappa, f, n: int, tol: float, leaf: int, precision: int = ACR_FP64, rtol=None,
+                       mem_budget: int = 0):
     """Differentiable solve u(log_kappa, f) on CUDA float64 tensors (see ACRSolve)."""
     global _ACRSolve
     if _ACRSolve is None:
         _ACRSolve = _autograd_function()
-    return _ACRSolve.apply(log_kappa, f, n, tol, leaf, precision, rtol)
+    return _ACRSolve.apply(log_kappa, f, n, tol, leaf, precision, rtol, mem_budget)

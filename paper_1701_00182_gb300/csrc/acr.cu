@@ -29,7 +29,6 @@ namespace acr {
 
 void* Ctx::dalloc_bytes(size_t bytes) {
   if (bytes == 0) return nullptr;
-  if (budget && live_bytes + bytes > budget) throw AcrError(ACR_ERR_OOM, "memory budget exceeded");
   void* p = nullptr;
   cudaError_t e = cudaMallocAsync(&p, bytes, st);
   if (e != cudaSuccess) {
@@ -132,9 +131,15 @@ struct LevelF {
 template <class T>
 struct FactorT {
   int q = 0;
+  // Levels r0..q-1 and the coarsest plane are not kept (memory budget): they
+  // are recomputed from the checkpoint of level r0's inputs (re-assembled from
+  // kappa when r0 = 0) for every solve call, and freed after it.  -1: all kept.
+  int r0 = -1;
+  int tail_pins = 0;  // > 0 while a call holds the recomputed levels
   std::vector<LevelF<T>> lv;
   HStore<T> Xc;
   DBuf<double> Xdense;  // FP64 dense inverse of the coarsest plane (m <= coarse_dense_max)
+  HStore<T> ckD, ckE, ckF;
   DBuf<T> Fint, tmp;
   int cap = 0;
   std::vector<std::pair<long, cudaGraphExec_t>> graphs;  // key nrhs*2 + transpose
@@ -157,6 +162,7 @@ struct acr_handle_s {
   DBuf<int> perm, iperm;
   std::vector<DBuf<int>> cutp, cutq;
   DBuf<double> kappa, coef, vel;
+  long long tail_recomputes = 0;
   std::unique_ptr<FactorT<float>> f32;
   std::unique_ptr<FactorT<double>> f64;
   acr_stats stats{};
@@ -250,14 +256,15 @@ void expand_dense_device(Ctx& c, const HMat<T>& A1, T* d) {
   }
 }
 
+// Level-0 blocks of the operator (Eq. originalMatrix) in HODLR form.
 template <class T>
-void factor_impl(acr_handle_s* h, FactorT<T>& fac) {
+void assemble_inputs(acr_handle_s* h, HStore<T>& D, HStore<T>& E, HStore<T>& F) {
   Ctx& c = h->ctx;
   const Geometry& g = h->geo;
   const int n = g.n, m = g.m, L = g.L, b = g.leaf;
-  const double tol = h->tol;
-  const bool exact = !(tol > 0);
-  HStore<T> D, E, F;
+  D = HStore<T>();
+  E = HStore<T>();
+  F = HStore<T>();
   D.leaf = DBuf<T>(c, (size_t)n * m * b);
   E.leaf = DBuf<T>(c, (size_t)n * m * b);
   F.leaf = DBuf<T>(c, (size_t)n * m * b);
@@ -275,73 +282,99 @@ void factor_impl(acr_handle_s* h, FactorT<T>& fac) {
     cq.push_back(h->cutq[l].p);
   }
   assemble_level0<T>(c, g, h->kappa.p, h->vel.p, h->shift, h->perm.p, h->iperm.p, cp, cq, D.h, E.h, F.h);
-  for (int l = 0; l < L; ++l) h->stats.max_rank_d[0][l] = g.ncut[l];
-  cudaEvent_t e0, e1;
-  ACR_CUDA(cudaEventCreate(&e0));
-  ACR_CUDA(cudaEventCreate(&e1));
-  int r = 0;
-  while (D.h.P > 1) {
-    ACR_CUDA(cudaEventRecord(e0, c.st));
-    LevelF<T> lvf;
-    const int nr = D.h.P, ne = nr / 2;
-    lvf.nr = nr;
-    lvf.ne = ne;
-    int rk[MAXL] = {};
-    {
-      WSum<T> ws = winverse<T>(c, D.h.sub(0, 2, ne));
-      lvf.X = wsum_to_hodlr<T>(c, ws, tol, exact, rk);
-      max_into(h->stats.max_rank[r], rk, L);
-    }
-    {
-      Flat<T> fg;
-      flat_init<T>(c, fg, ne, m, L, b);
-      flat_add_product<T>(c, fg, E.h.sub(1, 2, ne), lvf.X.h, T(1));
-      lvf.G = flat_finalize<T>(c, fg, tol, exact, nullptr);
-    }
-    if (ne > 1) {
-      Flat<T> fh;
-      flat_init<T>(c, fh, ne - 1, m, L, b);
-      flat_add_product<T>(c, fh, F.h.sub(1, 2, ne - 1), lvf.X.h.sub(1, 1, ne - 1), T(1));
-      lvf.H = flat_finalize<T>(c, fh, tol, exact, nullptr);
-    }
-    HStore<T> Dn, En, Fn;
-    {
-      Flat<T> fd;
-      flat_init<T>(c, fd, ne, m, L, b);
-      flat_add_hodlr<T>(c, fd, D.h.sub(1, 2, ne), T(1));
-      flat_add_product<T>(c, fd, lvf.G.h, F.h.sub(0, 2, ne), T(-1));
-      if (ne > 1) flat_add_product<T>(c, fd, lvf.H.h, E.h.sub(2, 2, ne - 1), T(-1));
-      Dn = flat_finalize<T>(c, fd, tol, exact, rk);
-      max_into(h->stats.max_rank_d[r + 1], rk, L);
-    }
-    {
-      Flat<T> fe;
-      flat_init<T>(c, fe, ne, m, L, b);
-      flat_add_product<T>(c, fe, lvf.G.h, E.h.sub(0, 2, ne), T(-1));
-      En = flat_finalize<T>(c, fe, tol, exact, nullptr);
-    }
-    {
-      Flat<T> ff;
-      flat_init<T>(c, ff, ne, m, L, b);
-      if (ne > 1) flat_add_product<T>(c, ff, lvf.H.h, F.h.sub(2, 2, ne - 1), T(-1));
-      Fn = flat_finalize<T>(c, ff, tol, exact, nullptr);
-    }
-    D = HStore<T>();
-    lvf.E = std::move(E);
-    lvf.F = std::move(F);
-    fac.lv.push_back(std::move(lvf));
-    D = std::move(Dn);
-    E = std::move(En);
-    F = std::move(Fn);
-    ACR_CUDA(cudaEventRecord(e1, c.st));
-    ACR_CUDA(cudaEventSynchronize(e1));
-    float ms = 0;
-    ACR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (r < 16) h->stats.t_level_ms[r] = ms;
-    ++r;
+}
+
+// Device copy of a batch of HODLR matrices (the checkpoint of a level's inputs).
+template <class T>
+HStore<T> hstore_clone(Ctx& c, const HStore<T>& A) {
+  HStore<T> B;
+  B.h = A.h;
+  const HMat<T>& a = A.h;
+  if (a.P <= 0) return B;
+  B.leaf = DBuf<T>(c, (size_t)a.P * a.m * a.b);
+  copy2d<T>(c, 1, (long)a.P * a.m, a.b, T(1), a.leaf, a.b, 0, B.leaf.p, a.b, 0);
+  for (int l = 0; l < a.L; ++l) {
+    const int K = a.K[l];
+    if (!K) continue;
+    B.U[l] = DBuf<T>(c, (size_t)a.P * a.m * K);
+    B.V[l] = DBuf<T>(c, (size_t)a.P * a.m * K);
+    copy2d<T>(c, 1, (long)a.P * a.m, K, T(1), a.U[l], K, 0, B.U[l].p, K, 0);
+    copy2d<T>(c, 1, (long)a.P * a.m, K, T(1), a.V[l], K, 0, B.V[l].p, K, 0);
   }
+  hstore_finish(B, a.P, a.m, a.L, a.b);
+  return B;
+}
+
+// One CR level (Eq. elim): the inverses of the eliminated planes, G and H of
+// the kept planes, and the next level's D, E, F.  The level's E and F move
+// into the stored factors.
+template <class T>
+void eliminate_level(acr_handle_s* h, int r, HStore<T>& D, HStore<T>& E, HStore<T>& F, LevelF<T>& lvf) {
+  Ctx& c = h->ctx;
+  const Geometry& g = h->geo;
+  const int m = g.m, L = g.L, b = g.leaf;
+  const double tol = h->tol;
+  const bool exact = !(tol > 0);
+  const int nr = D.h.P, ne = nr / 2;
+  lvf.nr = nr;
+  lvf.ne = ne;
+  int rk[MAXL] = {};
+  {
+    WSum<T> ws = winverse<T>(c, D.h.sub(0, 2, ne));
+    lvf.X = wsum_to_hodlr<T>(c, ws, tol, exact, rk);
+    max_into(h->stats.max_rank[r], rk, L);
+  }
+  {
+    Flat<T> fg;
+    flat_init<T>(c, fg, ne, m, L, b);
+    flat_add_product<T>(c, fg, E.h.sub(1, 2, ne), lvf.X.h, T(1));
+    lvf.G = flat_finalize<T>(c, fg, tol, exact, nullptr);
+  }
+  if (ne > 1) {
+    Flat<T> fh;
+    flat_init<T>(c, fh, ne - 1, m, L, b);
+    flat_add_product<T>(c, fh, F.h.sub(1, 2, ne - 1), lvf.X.h.sub(1, 1, ne - 1), T(1));
+    lvf.H = flat_finalize<T>(c, fh, tol, exact, nullptr);
+  }
+  HStore<T> Dn, En, Fn;
+  {
+    Flat<T> fd;
+    flat_init<T>(c, fd, ne, m, L, b);
+    flat_add_hodlr<T>(c, fd, D.h.sub(1, 2, ne), T(1));
+    flat_add_product<T>(c, fd, lvf.G.h, F.h.sub(0, 2, ne), T(-1));
+    if (ne > 1) flat_add_product<T>(c, fd, lvf.H.h, E.h.sub(2, 2, ne - 1), T(-1));
+    Dn = flat_finalize<T>(c, fd, tol, exact, rk);
+    max_into(h->stats.max_rank_d[r + 1], rk, L);
+  }
+  {
+    Flat<T> fe;
+    flat_init<T>(c, fe, ne, m, L, b);
+    flat_add_product<T>(c, fe, lvf.G.h, E.h.sub(0, 2, ne), T(-1));
+    En = flat_finalize<T>(c, fe, tol, exact, nullptr);
+  }
+  {
+    Flat<T> ff;
+    flat_init<T>(c, ff, ne, m, L, b);
+    if (ne > 1) flat_add_product<T>(c, ff, lvf.H.h, F.h.sub(2, 2, ne - 1), T(-1));
+    Fn = flat_finalize<T>(c, ff, tol, exact, nullptr);
+  }
+  D = HStore<T>();
+  lvf.E = std::move(E);
+  lvf.F = std::move(F);
+  D = std::move(Dn);
+  E = std::move(En);
+  F = std::move(Fn);
+}
+
+// Inverse of the coarsest plane (Eq. first_backSubs): dense FP64 when small
+// enough, else the HODLR inverse in the working precision.
+template <class T>
+void coarsest(acr_handle_s* h, FactorT<T>& fac, HStore<T>& D, int r) {
+  Ctx& c = h->ctx;
+  const int m = h->geo.m, L = h->geo.L;
+  const double tol = h->tol;
+  const bool exact = !(tol > 0);
   if (m <= h->coarse_dense_max) {
-    // Coarsest plane small enough for a dense FP64 factorisation (Eq. first_backSubs).
     DBuf<T> dT(c, (size_t)m * m);
     expand_dense_device<T>(c, D.h, dT.p);
     DBuf<double> dD(c, (size_t)m * m);
@@ -356,18 +389,130 @@ void factor_impl(acr_handle_s* h, FactorT<T>& fac) {
     fac.Xc = wsum_to_hodlr<T>(c, ws, tol, exact, rk);
     max_into(h->stats.max_rank[r], rk, L);
   }
+}
+
+template <class T>
+long level_bytes(const LevelF<T>& l) {
+  return l.X.h.bytes() + l.E.h.bytes() + l.F.h.bytes() + l.G.h.bytes() + l.H.h.bytes();
+}
+
+template <class T>
+void factor_impl(acr_handle_s* h, FactorT<T>& fac) {
+  Ctx& c = h->ctx;
+  const Geometry& g = h->geo;
+  const int n = g.n, m = g.m, L = g.L;
+  HStore<T> D, E, F;
+  assemble_inputs<T>(h, D, E, F);
+  for (int l = 0; l < L; ++l) h->stats.max_rank_d[0][l] = g.ncut[l];
+  cudaEvent_t e0, e1;
+  ACR_CUDA(cudaEventCreate(&e0));
+  ACR_CUDA(cudaEventCreate(&e1));
+  // Memory budget: level r is kept when the store, its estimate (twice the
+  // level's inputs) and a checkpoint of the next level's inputs (estimated as
+  // the level's own inputs) fit.  From the first level that does not, only the
+  // checkpoint of its inputs is kept, or nothing (the tail then starts at level
+  // 0, re-assembled from kappa) when even that would not fit; those levels are
+  // still computed here (ranks, breakdown checks) but not kept.  The store
+  // never exceeds the budget.
+  const long budget = (long)c.budget;
+  long stored = 0;
+  auto drop_from = [&](int r, HStore<T>& D, HStore<T>& E, HStore<T>& F) {
+    const long inputs = D.h.bytes() + E.h.bytes() + F.h.bytes();
+    if (r > 0 && stored + inputs <= budget) {
+      fac.r0 = r;
+      fac.ckD = hstore_clone<T>(c, D);
+      fac.ckE = hstore_clone<T>(c, E);
+      fac.ckF = hstore_clone<T>(c, F);
+    } else {
+      fac.r0 = 0;
+      fac.lv.clear();
+      stored = 0;
+    }
+  };
+  int r = 0;
+  while (D.h.P > 1) {
+    if (budget && fac.r0 < 0 && stored + 3 * (D.h.bytes() + E.h.bytes() + F.h.bytes()) > budget)
+      drop_from(r, D, E, F);
+    ACR_CUDA(cudaEventRecord(e0, c.st));
+    LevelF<T> lvf;
+    eliminate_level<T>(h, r, D, E, F, lvf);
+    if (fac.r0 < 0) {
+      stored += level_bytes(lvf);
+      fac.lv.push_back(std::move(lvf));
+      if (budget && stored > budget) {  // the estimate was short: keep nothing
+        fac.r0 = 0;
+        fac.lv.clear();
+        stored = 0;
+      }
+    }
+    ACR_CUDA(cudaEventRecord(e1, c.st));
+    ACR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    ACR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (r < 16) h->stats.t_level_ms[r] = ms;
+    ++r;
+  }
   fac.q = r;
+  if (fac.r0 < 0 && budget) {
+    const long m2 = (long)m * m;
+    const long est = m <= h->coarse_dense_max ? 8 * m2 : 2 * D.h.bytes();
+    if (stored + est > budget) drop_from(r, D, E, F);  // r0 = q: only the coarsest plane is recomputed
+  }
+  if (fac.r0 < 0) coarsest<T>(h, fac, D, r);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   check_flag(h);
+  h->stats.levels_stored = fac.r0 < 0 ? fac.q : fac.r0;
   fac.cap = h->nrhs_max;
   fac.Fint = DBuf<T>(c, (size_t)n * m * fac.cap);
   fac.tmp = DBuf<T>(c, (size_t)std::max(1, n / 2) * m * fac.cap);
 }
 
+// Recompute the levels r0..q-1 and the coarsest plane from the checkpoint
+// (held until tail_release).
+template <class T>
+void tail_acquire(acr_handle_s* h, FactorT<T>& fac) {
+  if (fac.r0 < 0 || fac.tail_pins++ > 0) return;
+  Ctx& c = h->ctx;
+  try {
+    HStore<T> D, E, F;
+    if (fac.r0 == 0) {
+      assemble_inputs<T>(h, D, E, F);
+    } else {
+      D = hstore_clone<T>(c, fac.ckD);
+      E = hstore_clone<T>(c, fac.ckE);
+      F = hstore_clone<T>(c, fac.ckF);
+    }
+    int r = fac.r0;
+    while (D.h.P > 1) {
+      LevelF<T> lvf;
+      eliminate_level<T>(h, r, D, E, F, lvf);
+      fac.lv.push_back(std::move(lvf));
+      ++r;
+    }
+    coarsest<T>(h, fac, D, r);
+    check_flag(h);
+  } catch (...) {
+    fac.lv.resize(fac.r0);
+    fac.Xc = HStore<T>();
+    fac.Xdense.release();
+    fac.tail_pins = 0;
+    throw;
+  }
+  h->tail_recomputes++;
+}
+
+template <class T>
+void tail_release(FactorT<T>& fac) {
+  if (fac.r0 < 0 || --fac.tail_pins > 0) return;
+  fac.lv.resize(fac.r0);
+  fac.Xc = HStore<T>();
+  fac.Xdense.release();
+}
+
 template <class T>
 long factor_bytes(const FactorT<T>& f) {
-  long s = f.Xc.h.bytes() + (long)f.Xdense.n * 8;
+  long s = f.Xc.h.bytes() + (long)f.Xdense.n * 8 + f.ckD.h.bytes() + f.ckE.h.bytes() + f.ckF.h.bytes();
   for (auto& l : f.lv) s += l.X.h.bytes() + l.E.h.bytes() + l.F.h.bytes() + l.G.h.bytes() + l.H.h.bytes();
   return s;
 }
@@ -456,7 +601,13 @@ void solve_impl(acr_handle_s* h, FactorT<T>& fac, const double* rhs, double* x, 
     tmp = Town.p;
   }
   permute_in<T>(c, n, nrhs, rhs, ld, h->perm.p, Fint);
-  if (h->graphs && !own && c.st) {
+  struct Pin {
+    acr_handle_s* h;
+    FactorT<T>& f;
+    Pin(acr_handle_s* hh, FactorT<T>& ff) : h(hh), f(ff) { tail_acquire<T>(h, f); }
+    ~Pin() { tail_release<T>(f); }
+  } pin(h, fac);
+  if (h->graphs && !own && c.st && fac.r0 < 0) {
     const long key = 2L * nrhs + (trans ? 1 : 0);
     cudaGraphExec_t ex = nullptr;
     for (auto& g : fac.graphs)
@@ -508,6 +659,19 @@ void publish_profile(acr_handle_s* h) {
     h->stats.kc_launches[k] = h->ctx.kc_launch[k];
   }
 }
+
+// Holds the recomputed levels of a budgeted factorisation for one call.
+struct TailPin {
+  acr_handle_s* h;
+  explicit TailPin(acr_handle_s* hh) : h(hh) {
+    if (h->f64) tail_acquire<double>(h, *h->f64);
+    else tail_acquire<float>(h, *h->f32);
+  }
+  ~TailPin() {
+    if (h->f64) tail_release<double>(*h->f64);
+    else tail_release<float>(*h->f32);
+  }
+};
 
 void solve_any(acr_handle_s* h, const double* rhs, double* x, int nrhs, long ld, bool trans, bool acc) {
   if (h->f64) solve_impl<double>(h, *h->f64, rhs, x, nrhs, ld, trans, acc);
@@ -579,6 +743,7 @@ int solve_ir_impl(acr_handle h, const double* b, double* x, int nrhs, long ld, d
     h->ctx.launches = 0;
     const long N = (long)h->n * h->n * h->n;
     DBuf<double> r(c, (size_t)ld * nrhs), nrm(c, 2 * (size_t)nrhs);
+    TailPin pin(h);
     ACR_CUDA(cudaMemset2DAsync(x, ld * sizeof(double), 0, N * sizeof(double), nrhs, c.st));
     ACR_CUDA(cudaMemcpy2DAsync(r.p, ld * sizeof(double), b, ld * sizeof(double), N * sizeof(double), nrhs,
                                cudaMemcpyDeviceToDevice, c.st));
@@ -631,7 +796,7 @@ const char* acr_error_string(int s) {
   switch (s) {
     case ACR_OK: return "ok";
     case ACR_ERR_ARG: return "invalid argument";
-    case ACR_ERR_OOM: return "out of device memory or memory budget";
+    case ACR_ERR_OOM: return "out of device memory";
     case ACR_ERR_BREAKDOWN: return "numerical breakdown (zero pivot)";
     case ACR_ERR_RANK_CAP: return "block rank above the cap";
     case ACR_ERR_CUDA: return "CUDA runtime error";
@@ -858,6 +1023,7 @@ int acr_solve_fgmres(acr_handle h, const double* b, double* x, int nrhs, long ld
     // Krylov basis V_0..V_m and preconditioned directions Z_0..Z_{m-1}, each N x nrhs (ld N).
     DBuf<double> Vb(c, (size_t)(mrs + 1) * N * nrhs), Zb(c, (size_t)mrs * N * nrhs), w(c, (size_t)N * nrhs);
     DBuf<double> nrm(c, 2 * (size_t)nrhs), dv(c, (size_t)nrhs), coefd(c, (size_t)nrhs);
+    TailPin pin(h);
     auto Vk = [&](int k) { return Vb.p + (size_t)k * N * nrhs; };
     auto Zk = [&](int k) { return Zb.p + (size_t)k * N * nrhs; };
     ACR_CUDA(cudaMemset2DAsync(x, ld * sizeof(double), 0, N * sizeof(double), nrhs, c.st));
@@ -976,6 +1142,7 @@ int acr_solve_fgmres(acr_handle h, const double* b, double* x, int nrhs, long ld
 int acr_get_factor_block(acr_handle h, int which, int level, int index, double* dense) {
   if (!h || !dense) return ACR_ERR_ARG;
   return guard([&] {
+    TailPin pin(h);
     if (h->f64) get_block_impl<double>(h, *h->f64, which, level, index, dense);
     else get_block_impl<float>(h, *h->f32, which, level, index, dense);
   });
@@ -983,6 +1150,7 @@ int acr_get_factor_block(acr_handle h, int which, int level, int index, double* 
 
 int acr_get_stats(acr_handle h, acr_stats* s) {
   if (!h || !s) return ACR_ERR_ARG;
+  h->stats.tail_recomputes = h->tail_recomputes;
   *s = h->stats;
   return ACR_OK;
 }

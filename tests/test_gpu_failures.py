@@ -52,10 +52,33 @@ def test_rank_cap(acr):
     _still_works(acr)
 
 
-def test_memory_budget(acr):
-    g = synthetic.gaussian_random_field(16, 1)
-    st = _status(acr, lambda: acr.acr_factor(16, g, 1e-6, 16, mem_budget=1 << 20))
+def test_device_allocation_failure_is_oom(acr):
+    """A solve workspace far beyond the device's memory: the allocation fails,
+    acr_factor returns ACR_ERR_OOM and frees what it had."""
+    g = synthetic.gaussian_random_field(64, 1)
+    st = _status(acr, lambda: acr.acr_factor(64, g, 1e-6, 64, precision=acr.ACR_FP32, nrhs_max=1 << 22))
     assert st == acr.ACR_ERR_OOM
+    _still_works(acr)
+
+
+def test_tiny_memory_budget_recomputes_everything(acr):
+    """A budget too small for any level keeps nothing: every solve call
+    re-assembles from kappa and recomputes all levels, with the same result."""
+    n = 16
+    g = synthetic.gaussian_random_field(n, 1)
+    f = synthetic.uniform_rhs(n, 0)
+    h0 = acr.acr_factor(n, g, 1e-6, 16)
+    h1 = acr.acr_factor(n, g, 1e-6, 16, mem_budget=1 << 10)
+    s = acr.acr_get_stats(h1)
+    assert s["levels_stored"] == 0 and s["factor_bytes"] == 0
+    b = to_cols(f)
+    x0, x1 = empty_like_cols(b), empty_like_cols(b)
+    acr.acr_solve(h0, b, x0)
+    acr.acr_solve(h1, b, x1)
+    acr.acr_solve_transpose(h1, b, x1)
+    acr.acr_solve(h1, b, x1)
+    np.testing.assert_array_equal(from_cols(x1), from_cols(x0))
+    assert acr.acr_get_stats(h1)["tail_recomputes"] == 3
     _still_works(acr)
 
 

@@ -303,6 +303,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=4.0, help="seconds of CPU work per reference-arm step")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e", type=int, default=1, help="also time the end-to-end host-buffer path")
+    ap.add_argument("--profiler-range", type=int, default=0,
+                    help="1: bracket the first timed step with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)
@@ -367,8 +369,13 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for i in range(args.steps):
+            if args.profiler_range and i == 0:
+                torch.cuda.profiler.start()
             it, rel, st, s = step()
+            if args.profiler_range and i == 0:
+                torch.cuda.synchronize()
+                torch.cuda.profiler.stop()
             iters.append(it)
             worst = max(worst, float(np.max(rel)))
             launches += sum(v["launches"] for v in s["kernels"].values())

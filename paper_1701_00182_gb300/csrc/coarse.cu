@@ -1,14 +1,17 @@
 // Dense FP64 factorisation of the coarsest plane (Eq. first_backSubs): the
 // single block D^{(q)} left after the last reduction step is small enough to
-// be factorised directly.  LU with partial pivoting, one pivot column at a
-// time (pivot search, row swap + column scaling, rank-one trailing update,
-// each a multi-CTA kernel whose traffic is the trailing matrix), then the
-// explicit inverse from two triangular solves with the identity, so that the
-// solve phase applies it as one FP64 product.
+// be factorised directly.  Blocked right-looking LU with partial pivoting
+// (panels of 64 columns: the panel is factorised by one CTA, its row swaps are
+// applied to the other columns, U12 comes from a unit-lower triangular solve,
+// and the trailing block is updated by one FP64 GEMM), then the explicit
+// inverse from A X = P by blocked forward and backward substitution (a
+// triangular solve per diagonal block, a GEMM per off-diagonal update), so
+// that the solve phase applies it as one FP64 product.
 #include <algorithm>
 #include <cmath>
 
 #include "acr_internal.h"
+#include "hodlr.cuh"
 
 namespace acr {
 
@@ -17,131 +20,175 @@ inline int nblk(long tot, int bs = 256, int cap = 152 * 32) {
   long b = (tot + bs - 1) / bs;
   return (int)std::max(1L, std::min<long>(b, cap));
 }
+constexpr int kNB = 64;  // panel width
 }  // namespace
 
-// piv[k] = argmax_{r >= k} |A[r][k]| (one CTA).
-__global__ void k_lu_pivot(int m, int k, const double* A, int* piv) {
-  __shared__ double bv[1024];
-  __shared__ int bi[1024];
-  double best = -1.0;
-  int idx = k;
-  for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
-    double v = fabs(A[(long)r * m + k]);
-    if (v > best) { best = v; idx = r; }
-  }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = idx;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s && (bv[threadIdx.x + s] > bv[threadIdx.x] ||
-                            (bv[threadIdx.x + s] == bv[threadIdx.x] && bi[threadIdx.x + s] < bi[threadIdx.x]))) {
-      bv[threadIdx.x] = bv[threadIdx.x + s];
-      bi[threadIdx.x] = bi[threadIdx.x + s];
+// LU with partial pivoting of the panel rows k0..m-1, columns k0..k0+jb-1 of
+// A (row major, ld m), one CTA: piv[k0 + j] = the row swapped with k0 + j.
+// Multipliers are stored below the diagonal; a zero pivot sets flag and is
+// replaced by a tiny one.
+__global__ void __launch_bounds__(1024) k_panel_lu(int m, int k0, int jb, double* A, int* piv, int* flag) {
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  __shared__ double prow[kNB];
+  __shared__ int s_p;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < jb; ++j) {
+    const int col = k0 + j;
+    double best = -1.0;
+    int idx = 0x7fffffff;
+    for (int r = col + tid; r < m; r += blockDim.x) {
+      const double v = fabs(A[(long)r * m + col]);
+      if (v > best) { best = v; idx = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (ov > best || (ov == best && oi < idx)) { best = ov; idx = oi; }
+    }
+    if (lane == 0) { bv[warp] = best; bi[warp] = idx; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = -1.0;
+      int bb = col;
+      for (int w = 0; w < nw; ++w)
+        if (bv[w] > b || (bv[w] == b && bi[w] < bb)) { b = bv[w]; bb = bi[w]; }
+      s_p = bb;
+      piv[col] = bb;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != col && tid < jb) {
+      const double t = A[(long)col * m + k0 + tid];
+      A[(long)col * m + k0 + tid] = A[(long)p * m + k0 + tid];
+      A[(long)p * m + k0 + tid] = t;
+    }
+    __syncthreads();
+    if (tid < jb) prow[tid] = A[(long)col * m + k0 + tid];
+    __syncthreads();
+    double d = prow[j];
+    if (d == 0.0) {
+      if (tid == 0 && flag) atomicExch(flag, 1);
+      d = 1e-300;
+    }
+    const double id = 1.0 / d;
+    for (int r = col + 1 + tid; r < m; r += blockDim.x) {
+      double* ar = A + (long)r * m + k0;
+      const double l = ar[j] * id;
+      ar[j] = l;
+      for (int c2 = j + 1; c2 < jb; ++c2) ar[c2] -= l * prow[c2];
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) piv[k] = bi[0];
 }
 
-// Swap rows k and piv[k] (all m columns).
-__global__ void k_lu_swap(int m, int k, double* A, const int* piv) {
-  const int p = piv[k];
-  if (p == k) return;
+// Row swaps k0..k0+jb-1 (in order) applied to the columns outside the panel.
+__global__ void k_swap_rows(int m, int k0, int jb, double* A, const int* piv) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-    double t = A[(long)k * m + j];
-    A[(long)k * m + j] = A[(long)p * m + j];
-    A[(long)p * m + j] = t;
-  }
-}
-
-// L multipliers of column k and the rank-one update of the trailing block.
-// The multipliers are formed from the unscaled column inside the update, so
-// one launch suffices; a zero pivot sets flag and is replaced by a tiny one.
-__global__ void k_lu_update(int m, int k, double* A, int* flag) {
-  const double d0 = A[(long)k * m + k];
-  const double d = (d0 != 0.0) ? d0 : 1e-300;
-  if (d0 == 0.0 && blockIdx.x == 0 && threadIdx.x == 0 && flag) atomicExch(flag, 1);
-  const long rows = m - k - 1, cols = m - k - 1;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < rows * (cols + 1); e += (long)gridDim.x * blockDim.x) {
-    const long r = k + 1 + e / (cols + 1);
-    const long cj = e % (cols + 1);  // 0: the multiplier itself, else trailing column k + cj
-    const double l = A[r * m + k] / d;
-    if (cj == 0) continue;
-    A[r * m + k + cj] -= l * A[(long)k * m + k + cj];
-  }
-}
-
-__global__ void k_lu_scale(int m, int k, double* A) {
-  const double d = A[(long)k * m + k];
-  for (int r = k + 1 + blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x)
-    A[(long)r * m + k] = (d != 0.0) ? A[(long)r * m + k] / d : 0.0;
-}
-
-// X <- P X (apply the recorded row interchanges, in order, to an m x m matrix).
-__global__ void k_lu_apply_piv(int m, double* X, const int* piv) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x)
-    for (int k = 0; k < m; ++k) {
-      int p = piv[k];
-      if (p != k) {
-        double t = X[(long)k * m + j];
-        X[(long)k * m + j] = X[(long)p * m + j];
-        X[(long)p * m + j] = t;
+    if (j >= k0 && j < k0 + jb) continue;
+    for (int i = k0; i < k0 + jb; ++i) {
+      const int p = piv[i];
+      if (p != i) {
+        const double t = A[(long)i * m + j];
+        A[(long)i * m + j] = A[(long)p * m + j];
+        A[(long)p * m + j] = t;
       }
     }
-}
-
-// Forward step k of L Y = X (unit lower): rows below k lose L[r][k] * Y[k][:].
-__global__ void k_lu_fwd(int m, int k, const double* LU, double* X) {
-  const long rows = m - k - 1;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < rows * m; e += (long)gridDim.x * blockDim.x) {
-    const long r = k + 1 + e / m, j = e % m;
-    X[r * m + j] -= LU[r * m + k] * X[(long)k * m + j];
   }
 }
 
-// Backward step k of U Z = Y: row k is divided by U[k][k], rows above lose U[r][k] * Z[k][:].
-__global__ void k_lu_bwd_scale(int m, int k, const double* LU, double* X) {
-  const double d = LU[(long)k * m + k];
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) X[(long)k * m + j] /= d;
+// B rows k0..k0+jb-1, columns c0.. (one thread per column) <- L11^{-1} B with
+// L11 the unit lower block of T at (k0, k0) (upper = false), or U11^{-1} B
+// with U11 its upper block, diagonal included (upper = true).
+__global__ void __launch_bounds__(256) k_trsm_block(int m, int k0, int jb, const double* T, double* B, int c0,
+                                                    int ncols, int upper) {
+  __shared__ double t11[kNB][kNB + 1];
+  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) t11[e / jb][e % jb] = T[(long)(k0 + e / jb) * m + k0 + e % jb];
+  __syncthreads();
+  for (int j = c0 + blockIdx.x * blockDim.x + threadIdx.x; j < c0 + ncols; j += gridDim.x * blockDim.x) {
+    double* bj = B + (long)k0 * m + j;
+    if (!upper) {
+      for (int i = 1; i < jb; ++i) {
+        double v = bj[(long)i * m];
+        for (int t = 0; t < i; ++t) v -= t11[i][t] * bj[(long)t * m];
+        bj[(long)i * m] = v;
+      }
+    } else {
+      for (int i = jb - 1; i >= 0; --i) {
+        double v = bj[(long)i * m];
+        for (int t = i + 1; t < jb; ++t) v -= t11[i][t] * bj[(long)t * m];
+        bj[(long)i * m] = v / t11[i][i];
+      }
+    }
+  }
 }
-__global__ void k_lu_bwd(int m, int k, const double* LU, double* X) {
-  const long rows = k;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < rows * m; e += (long)gridDim.x * blockDim.x) {
-    const long r = e / m, j = e % m;
-    X[r * m + j] -= LU[r * m + k] * X[(long)k * m + j];
+
+// X = P (the row interchanges applied to the identity): row i of X is e_{perm[i]}.
+__global__ void k_perm_identity(int m, const int* piv, int* perm, double* X) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int i = 0; i < m; ++i) perm[i] = i;
+    for (int k = 0; k < m; ++k) {
+      const int p = piv[k];
+      const int t = perm[k];
+      perm[k] = perm[p];
+      perm[p] = t;
+    }
+  }
+}
+__global__ void k_perm_fill(int m, const int* perm, double* X) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)m * m; e += (long)gridDim.x * blockDim.x) {
+    const long i = e / m, j = e % m;
+    X[e] = (perm[i] == j) ? 1.0 : 0.0;
   }
 }
 
 // Dense inverse of the m x m FP64 matrix A (overwritten by its LU factors).
 void dense_inverse_fp64(Ctx& c, int m, double* A, double* Xinv) {
-  DBuf<int> piv(c, m);
-  const int grid = 152 * 4;
-  for (int k = 0; k < m; ++k) {
+  DBuf<int> piv(c, m), perm(c, m);
+  const int cgrid = std::min(152 * 4, (m + 255) / 256);
+  for (int k0 = 0; k0 < m; k0 += kNB) {
+    const int jb = std::min(kNB, m - k0), rest = m - k0 - jb;
     c.kbegin();
-    k_lu_pivot<<<1, 1024, 0, c.st>>>(m, k, A, piv.p);
-    k_lu_swap<<<nblk(m), 256, 0, c.st>>>(m, k, A, piv.p);
-    k_lu_update<<<grid, 256, 0, c.st>>>(m, k, A, c.d_flag);
-    k_lu_scale<<<nblk(m), 256, 0, c.st>>>(m, k, A);
-    c.kend(KC_GJ, 2.0 * (double)(m - k - 1) * (m - k - 1), 16.0 * (double)(m - k) * (m - k));
-    c.launches += 3;
+    k_panel_lu<<<1, 1024, 0, c.st>>>(m, k0, jb, A, piv.p, c.d_flag);
+    k_swap_rows<<<cgrid, 256, 0, c.st>>>(m, k0, jb, A, piv.p);
+    if (rest > 0) k_trsm_block<<<(rest + 255) / 256, 256, 0, c.st>>>(m, k0, jb, A, A, k0 + jb, rest, 0);
+    c.kend(KC_GJ, (double)(m - k0) * jb * jb + (double)rest * jb * jb, 16.0 * (double)(m - k0) * jb);
+    c.launches += 2;
+    if (rest > 0) {
+      c.tag = "coarse_lu";
+      gemm<double>(c, rest, rest, jb, 1, 1, -1.0, opm<double>(A + (long)(k0 + jb) * m + k0, m, 1, 0, 0),
+                   opm<double>(A + (long)k0 * m + k0 + jb, m, 1, 0, 0), 1.0,
+                   opm<double>(A + (long)(k0 + jb) * m + k0 + jb, m, 1, 0, 0));
+    }
   }
-  // Xinv = U^{-1} L^{-1} P  by solving A X = I column-block-wise.
-  fill<double>(c, Xinv, (long)m * m, 0.0);
-  set_identity_clusters<double>(c, 1, m, m, Xinv, m, (long)m * m);
+  // Xinv = U^{-1} L^{-1} P: A X = P by blocked forward then backward substitution.
   c.kbegin();
-  k_lu_apply_piv<<<nblk(m), 256, 0, c.st>>>(m, Xinv, piv.p);
-  c.kend(KC_GJ, 0, 16.0 * (double)m * m);
-  for (int k = 0; k < m - 1; ++k) {
+  k_perm_identity<<<1, 32, 0, c.st>>>(m, piv.p, perm.p, Xinv);
+  k_perm_fill<<<nblk((long)m * m), 256, 0, c.st>>>(m, perm.p, Xinv);
+  c.kend(KC_GJ, 0, 8.0 * (double)m * m);
+  c.launches += 1;
+  const int tgrid = (m + 255) / 256;
+  for (int k0 = 0; k0 < m; k0 += kNB) {
+    const int jb = std::min(kNB, m - k0), rest = m - k0 - jb;
     c.kbegin();
-    k_lu_fwd<<<grid, 256, 0, c.st>>>(m, k, A, Xinv);
-    c.kend(KC_GJ, 2.0 * (double)(m - k - 1) * m, 24.0 * (double)(m - k - 1) * m);
+    k_trsm_block<<<tgrid, 256, 0, c.st>>>(m, k0, jb, A, Xinv, 0, m, 0);
+    c.kend(KC_GJ, (double)m * jb * jb, 16.0 * (double)m * jb);
+    if (rest > 0) {
+      c.tag = "coarse_inv";
+      gemm<double>(c, rest, m, jb, 1, 1, -1.0, opm<double>(A + (long)(k0 + jb) * m + k0, m, 1, 0, 0),
+                   opm<double>(Xinv + (long)k0 * m, m, 1, 0, 0), 1.0, opm<double>(Xinv + (long)(k0 + jb) * m, m, 1, 0, 0));
+    }
   }
-  for (int k = m - 1; k >= 0; --k) {
+  for (int k0 = (m - 1) / kNB * kNB; k0 >= 0; k0 -= kNB) {
+    const int jb = std::min(kNB, m - k0);
     c.kbegin();
-    k_lu_bwd_scale<<<nblk(m), 256, 0, c.st>>>(m, k, A, Xinv);
-    if (k > 0) k_lu_bwd<<<grid, 256, 0, c.st>>>(m, k, A, Xinv);
-    c.kend(KC_GJ, 2.0 * (double)k * m, 24.0 * (double)k * m);
-    c.launches += 1;
+    k_trsm_block<<<tgrid, 256, 0, c.st>>>(m, k0, jb, A, Xinv, 0, m, 1);
+    c.kend(KC_GJ, (double)m * jb * jb, 16.0 * (double)m * jb);
+    if (k0 > 0) {
+      c.tag = "coarse_inv";
+      gemm<double>(c, k0, m, jb, 1, 1, -1.0, opm<double>(A + k0, m, 1, 0, 0), opm<double>(Xinv + (long)k0 * m, m, 1, 0, 0),
+                   1.0, opm<double>(Xinv, m, 1, 0, 0));
+    }
   }
 }
 

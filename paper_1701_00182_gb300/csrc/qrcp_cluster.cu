@@ -47,8 +47,9 @@ struct Pub {
 
 }  // namespace
 
-// Shared memory per CTA: W (ldw x cw, column major), vloc (r), vpub (2 r),
-// taus (r), nrm and nrm0 (cw), chosen step tj (cw ints).
+// Shared memory per CTA: W (ldw x cw, column major: the local columns, later
+// Q's local columns), vloc (r), vpub (2 r), taus (r), nrm and nrm0 (cw),
+// chosen step tj (cw ints).
 //
 // One cluster barrier per step: before it, warp 0 of every CTA picks its best
 // remaining local column and publishes, besides its norm, that column's
@@ -206,12 +207,13 @@ __global__ void __launch_bounds__(kQT)
     __syncthreads();
     // apply H = I - tau v v^T to the remaining local columns; row st becomes
     // R's row st.  A warp's columns go in groups of four so that their dot
-    // products, reductions and updates overlap.
-    if (tau != T(0)) {
-      for (int jb = warp * 4; jb < ncl; jb += nw * 4) {
-        T w[4];
+    // products, reductions and updates overlap; the same warp then downdates
+    // their norms.
+    for (int jb = warp * 4; jb < ncl; jb += nw * 4) {
+      T w[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) w[u] = T(0);
+      for (int u = 0; u < 4; ++u) w[u] = T(0);
+      if (tau != T(0)) {
         for (int i = st + lane; i < kL; i += 32) {
           const T vi = vloc[i];
 #pragma unroll
@@ -230,21 +232,23 @@ __global__ void __launch_bounds__(kQT)
           for (int u = 0; u < 4; ++u)
             if (w[u] != T(0)) W[(long)(jb + u) * ldw + i] -= w[u] * vi;
         }
+        __syncwarp();
       }
-      __syncthreads();
-    }
-    for (int jl = warp; jl < ncl; jl += nw) {
-      if (tj[jl] >= 0) continue;
-      const T* cj = W + (long)jl * ldw;
-      T nn = nrm[jl] - cj[st] * cj[st];
-      if (nn < T(0.05) * nrm0[jl]) {  // the downdate lost its digits: recompute
-        T a = 0;
-        for (int i = st + 1 + lane; i < kL; i += 32) a += cj[i] * cj[i];
-        a = wred_sum(a);
-        if (lane == 0) nrm0[jl] = a;
-        nn = a;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int jl = jb + u;
+        if (jl >= ncl || tj[jl] >= 0) continue;  // uniform over the warp
+        const T* cj = W + (long)jl * ldw;
+        T nn = nrm[jl] - cj[st] * cj[st];
+        if (nn < T(0.05) * nrm0[jl]) {  // the downdate lost its digits: recompute
+          T a = 0;
+          for (int i = st + 1 + lane; i < kL; i += 32) a += cj[i] * cj[i];
+          a = wred_sum(a);
+          if (lane == 0) nrm0[jl] = a;
+          nn = a;
+        }
+        if (lane == 0) nrm[jl] = nn;
       }
-      if (lane == 0) nrm[jl] = nn;
     }
     __syncthreads();
     rank = st + 1;

@@ -51,6 +51,19 @@ __global__ void k_copy2d(int P, long rows, int cols, T alpha, const T* src, long
     for (; j < cols; j += 32) dr[j] = alpha * sr[j];
   }
 }
+// Narrow rows (cols < 32): one thread per element, 32-bit index arithmetic
+// (the caller checks the element count fits), so a warp covers several rows.
+template <class T>
+__global__ void k_copy2d_narrow(int P, int rows, int cols, T alpha, const T* __restrict__ src, long sld, long sps,
+                                T* __restrict__ dst, long dld, long dps) {
+  const unsigned tot = (unsigned)P * (unsigned)rows * (unsigned)cols;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+    const unsigned rw = e / (unsigned)cols, j = e - rw * (unsigned)cols;
+    const unsigned p = rw / (unsigned)rows, i = rw - p * (unsigned)rows;
+    dst[p * dps + i * dld + j] = alpha * src[p * sps + i * sld + j];
+  }
+}
+
 template <class T>
 void copy2d(Ctx& c, int P, long rows, int cols, T alpha, const T* src, long sld, long sps, T* dst, long dld,
             long dps) {
@@ -61,8 +74,11 @@ void copy2d(Ctx& c, int P, long rows, int cols, T alpha, const T* src, long sld,
     c.check_range(dst, 0, (long)(P - 1) * dps + (rows - 1) * dld + cols - 1, sizeof(T), "copy2d dst");
   }
   c.kbegin();
-  k_copy2d<T><<<nblk((long)P * rows * 32), 256, 0, c.st>>>(P, rows, cols, alpha, src, sld, sps, dst, dld, dps);
-  c.kend(KC_COPY, 0, 2.0 * sizeof(T) * tot, "copy:copy2d");
+  if (cols < 32 && tot < (1L << 31) && rows < (1L << 31))
+    k_copy2d_narrow<T><<<nblk(tot), 256, 0, c.st>>>(P, (int)rows, cols, alpha, src, sld, sps, dst, dld, dps);
+  else
+    k_copy2d<T><<<nblk((long)P * rows * 32), 256, 0, c.st>>>(P, rows, cols, alpha, src, sld, sps, dst, dld, dps);
+  c.kend(KC_COPY, 0, 2.0 * sizeof(T) * tot, c.site_detail ? (cols < 32 ? "copy:copy2d narrow" : "copy:copy2d") : "copy:copy2d");
 }
 
 // Every cluster (size s) of every plane: U|c = I_s  (panel of width s).

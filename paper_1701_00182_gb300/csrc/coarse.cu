@@ -1,7 +1,8 @@
 // Dense FP64 factorisation of the coarsest plane (Eq. first_backSubs): the
 // single block D^{(q)} left after the last reduction step is small enough to
 // be factorised directly.  Blocked right-looking LU with partial pivoting
-// (panels of 64 columns: the panel is factorised by one CTA, its row swaps are
+// (panels of 64 columns: each panel column is a pivot search + swap by one
+// CTA and a row-parallel update of the panel, the panel's row swaps are then
 // applied to the other columns, U12 comes from a unit-lower triangular solve,
 // and the trailing block is updated by one FP64 GEMM), then the explicit
 // inverse from A X = P by blocked forward and backward substitution (a
@@ -23,62 +24,61 @@ inline int nblk(long tot, int bs = 256, int cap = 152 * 32) {
 constexpr int kNB = 64;  // panel width
 }  // namespace
 
-// LU with partial pivoting of the panel rows k0..m-1, columns k0..k0+jb-1 of
-// A (row major, ld m), one CTA: piv[k0 + j] = the row swapped with k0 + j.
-// Multipliers are stored below the diagonal; a zero pivot sets flag and is
-// replaced by a tiny one.
-__global__ void __launch_bounds__(1024) k_panel_lu(int m, int k0, int jb, double* A, int* piv, int* flag) {
+// Column col of the panel (columns k0..k0+jb-1): piv[col] = argmax over rows
+// r >= col of |A[r][col]| (lowest index on ties), and rows col and piv[col]
+// swapped across the panel.  One CTA.
+__global__ void __launch_bounds__(1024) k_panel_pivot(int m, int col, int k0, int jb, double* A, int* piv) {
   __shared__ double bv[32];
   __shared__ int bi[32];
-  __shared__ double prow[kNB];
   __shared__ int s_p;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int j = 0; j < jb; ++j) {
-    const int col = k0 + j;
-    double best = -1.0;
-    int idx = 0x7fffffff;
-    for (int r = col + tid; r < m; r += blockDim.x) {
-      const double v = fabs(A[(long)r * m + col]);
-      if (v > best) { best = v; idx = r; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-      if (ov > best || (ov == best && oi < idx)) { best = ov; idx = oi; }
-    }
-    if (lane == 0) { bv[warp] = best; bi[warp] = idx; }
-    __syncthreads();
-    if (tid == 0) {
-      double b = -1.0;
-      int bb = col;
-      for (int w = 0; w < nw; ++w)
-        if (bv[w] > b || (bv[w] == b && bi[w] < bb)) { b = bv[w]; bb = bi[w]; }
-      s_p = bb;
-      piv[col] = bb;
-    }
-    __syncthreads();
-    const int p = s_p;
-    if (p != col && tid < jb) {
-      const double t = A[(long)col * m + k0 + tid];
-      A[(long)col * m + k0 + tid] = A[(long)p * m + k0 + tid];
-      A[(long)p * m + k0 + tid] = t;
-    }
-    __syncthreads();
-    if (tid < jb) prow[tid] = A[(long)col * m + k0 + tid];
-    __syncthreads();
-    double d = prow[j];
-    if (d == 0.0) {
-      if (tid == 0 && flag) atomicExch(flag, 1);
-      d = 1e-300;
-    }
-    const double id = 1.0 / d;
-    for (int r = col + 1 + tid; r < m; r += blockDim.x) {
-      double* ar = A + (long)r * m + k0;
-      const double l = ar[j] * id;
-      ar[j] = l;
-      for (int c2 = j + 1; c2 < jb; ++c2) ar[c2] -= l * prow[c2];
-    }
-    __syncthreads();
+  double best = -1.0;
+  int idx = 0x7fffffff;
+  for (int r = col + tid; r < m; r += blockDim.x) {
+    const double v = fabs(A[(long)r * m + col]);
+    if (v > best) { best = v; idx = r; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > best || (ov == best && oi < idx)) { best = ov; idx = oi; }
+  }
+  if (lane == 0) { bv[warp] = best; bi[warp] = idx; }
+  __syncthreads();
+  if (tid == 0) {
+    double b = -1.0;
+    int bb = col;
+    for (int w = 0; w < nw; ++w)
+      if (bv[w] > b || (bv[w] == b && bi[w] < bb)) { b = bv[w]; bb = bi[w]; }
+    s_p = bb;
+    piv[col] = bb;
+  }
+  __syncthreads();
+  const int p = s_p;
+  if (p != col && tid < jb) {
+    const double t = A[(long)col * m + k0 + tid];
+    A[(long)col * m + k0 + tid] = A[(long)p * m + k0 + tid];
+    A[(long)p * m + k0 + tid] = t;
+  }
+}
+
+// Rows below col: multiplier l = A[r][col] / A[col][col] stored in place and
+// the panel's remaining columns updated, one warp per row (lanes along the
+// row).  A zero pivot sets flag and is replaced by a tiny one.
+__global__ void k_panel_update(int m, int col, int k0, int jb, double* A, int* flag) {
+  const int lane = threadIdx.x & 31;
+  const double d0 = A[(long)col * m + col];
+  const double d = (d0 != 0.0) ? d0 : 1e-300;
+  if (d0 == 0.0 && blockIdx.x == 0 && threadIdx.x == 0 && flag) atomicExch(flag, 1);
+  const double* prow = A + (long)col * m;
+  const int c1 = k0 + jb;
+  for (long r = col + 1 + ((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5); r < m;
+       r += ((long)gridDim.x * blockDim.x) >> 5) {
+    double* ar = A + r * m;
+    const double l = ar[col] / d;  // every lane reads it before lane 0 overwrites it
+    __syncwarp();
+    for (int c2 = col + 1 + lane; c2 < c1; c2 += 32) ar[c2] -= l * prow[c2];
+    if (lane == 0) ar[col] = l;
   }
 }
 
@@ -149,7 +149,12 @@ void dense_inverse_fp64(Ctx& c, int m, double* A, double* Xinv) {
   for (int k0 = 0; k0 < m; k0 += kNB) {
     const int jb = std::min(kNB, m - k0), rest = m - k0 - jb;
     c.kbegin();
-    k_panel_lu<<<1, 1024, 0, c.st>>>(m, k0, jb, A, piv.p, c.d_flag);
+    for (int j = 0; j < jb; ++j) {
+      const int col = k0 + j, rows = m - col - 1;
+      k_panel_pivot<<<1, 1024, 0, c.st>>>(m, col, k0, jb, A, piv.p);
+      if (rows > 0) k_panel_update<<<std::max(1, std::min((rows + 7) / 8, 152 * 8)), 256, 0, c.st>>>(m, col, k0, jb, A, c.d_flag);
+    }
+    c.launches += 2 * jb;
     k_swap_rows<<<cgrid, 256, 0, c.st>>>(m, k0, jb, A, piv.p);
     if (rest > 0) k_trsm_block<<<(rest + 255) / 256, 256, 0, c.st>>>(m, k0, jb, A, A, k0 + jb, rest, 0);
     c.kend(KC_GJ, (double)(m - k0) * jb * jb + (double)rest * jb * jb, 16.0 * (double)(m - k0) * jb);

@@ -78,12 +78,16 @@ void Ctx::kend(int cls, double flops, double bytes, const char* name) {
 void Ctx::kflush() {
   if (pend.empty()) return;
   ACR_CUDA(cudaStreamSynchronize(st));
-  for (auto& p : pend) {
+  for (size_t i = 0; i < pend.size(); ++i) {
+    auto& p = pend[i];
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       kc_ms[p.cls] += ms;
       if (p.tag) site[p.tag].first += ms;
     }
+    // idle time of the stream between the previous launch and this one (host work, syncs)
+    if (site_detail && i > 0 && cudaEventElapsedTime(&ms, pend[i - 1].b, p.a) == cudaSuccess)
+      gap[p.tag ? std::string(p.tag) : "class " + std::to_string(p.cls)] += ms;
     evfree.push_back(p.a);
     evfree.push_back(p.b);
   }
@@ -183,6 +187,8 @@ struct acr_handle_s {
       for (auto& kv : ctx.site)
         std::fprintf(stderr, "acr gemm site %-14s %10.1f ms %10.3f TFLOP\n", kv.first.c_str(), kv.second.first,
                      kv.second.second / 1e12);
+      for (auto& kv : ctx.gap)
+        if (kv.second >= 1.0) std::fprintf(stderr, "acr idle before %-24s %10.1f ms\n", kv.first.c_str(), kv.second);
     }
     for (auto& p : ctx.pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     ctx.pend.clear();
@@ -613,7 +619,8 @@ void solve_impl(acr_handle_s* h, FactorT<T>& fac, const double* rhs, double* x, 
     for (auto& g : fac.graphs)
       if (g.first == key) ex = g.second;
     if (!ex) {
-      const bool prof = c.profile, tune = c.autotune, chk = c.check_bounds;
+      const bool prof = c.profile, tune = c.autotune, chk = c.check_bounds, ver = c.verify_gemm;
+      c.verify_gemm = false;  // no host synchronisation inside a capture
       c.profile = false;  // no event timing or host synchronisation inside a capture
       c.autotune = false;
       cudaGraph_t graph = nullptr;
@@ -625,12 +632,14 @@ void solve_impl(acr_handle_s* h, FactorT<T>& fac, const double* rhs, double* x, 
         if (graph) cudaGraphDestroy(graph);
         c.profile = prof;
         c.autotune = tune;
+        c.verify_gemm = ver;
         throw;
       }
       ACR_CUDA(cudaStreamEndCapture(c.st, &graph));
       c.profile = prof;
       c.autotune = tune;
       c.check_bounds = chk;
+      c.verify_gemm = ver;
       cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
       cudaGraphDestroy(graph);
       ACR_CUDA(e);
@@ -844,6 +853,11 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     c.budget = o.mem_budget;
     const char* cb = std::getenv("ACR_CHECK_BOUNDS");
     c.check_bounds = cb && cb[0] == '1';
+    const char* qr = std::getenv("ACR_QRCP_REG");
+    c.qrcp_reg = !(qr && qr[0] == '0');
+    c.qrcp_reg_all = qr && qr[0] == '2';
+    const char* gv = std::getenv("ACR_GEMM_VERIFY");
+    c.verify_gemm = gv && gv[0] == '1';
     const char* sd = std::getenv("ACR_PROFILE_SITES");
     c.site_detail = sd && sd[0] == '2';
     const char* fc = std::getenv("ACR_GEMM_CFG");

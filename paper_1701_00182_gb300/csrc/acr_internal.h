@@ -55,11 +55,14 @@ struct Ctx {
   bool autotune = false;
   std::map<uintptr_t, size_t> live;  // allocation start -> bytes (for the operand extent check)
   bool check_bounds = false;  // ACR_CHECK_BOUNDS=1: verify every GEMM operand range on the host
+  bool verify_gemm = false;   // ACR_GEMM_VERIFY=1: recompute every GEMM with the reference FMA tiling and report differences
   bool inverse_fp64 = false;  // FP32 factorisation: leaf and coupling inverses in FP64
   bool tensor = false;        // FP32 GEMMs of large tiles on the tensor cores (3xTF32)
   int force_cfg = -1;         // ACR_GEMM_CFG=<i>: every GEMM uses tiling i where it is valid (debugging)
   int chol_passes = 1;         // pivoted-Cholesky passes of the FP32 recompression (1 = Gram floor only)
   bool qrcp_cluster = true;    // pivoted QR of large cores / explicit blocks on a thread-block cluster
+  bool qrcp_reg = true;        // FP32 blocks up to 512 x 512: the register-resident cluster variant (ACR_QRCP_REG=0: off)
+  bool qrcp_reg_all = false;   // ACR_QRCP_REG=2: also the blocks that fit one CTA's shared memory
   int core_svd = 0;           // core truncation: 0 / 2 pivoted QR (default), 1 Jacobi SVD
   void check_range(const void* base, long lo, long hi, size_t es, const char* what) const;
   bool profile = false;  // record CUDA events around every launch, accumulated per kernel class
@@ -70,6 +73,7 @@ struct Ctx {
   bool site_detail = false;   // ACR_PROFILE_SITES=2: split each site by GEMM shape and tiling
   std::set<std::string> tagstore;
   std::map<std::string, std::pair<double, double>> site;  // tag -> (ms, flops)
+  std::map<std::string, double> gap;  // tag (or class) of a launch -> device idle time before it (ms)
   std::vector<cudaEvent_t> evfree;
   std::vector<PendingEv> pend;
   cudaEvent_t evcur = nullptr;

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "acr_internal.h"
@@ -622,13 +623,19 @@ namespace {
 struct Cfg {
   int bm, bn, bk;
 };
-constexpr int kNCfg = 8;
+constexpr int kNCfg = 12;
 constexpr Cfg kCfg[kNCfg] = {{64, 64, 16},   {128, 64, 8},   {32, 32, 32},   {128, 128, 8},
-                             {128, 128, 8}, {128, 128, 16}, {128, 128, 32}, {128, 128, 32}};
+                             {128, 128, 8},  {128, 128, 16}, {128, 128, 32}, {128, 128, 32},
+                             {32, 1024, 32}, {64, 64, 16},   {64, 128, 16},  {128, 64, 16}};
 
 // Configurations 5 (mma.sync 3xTF32), 6 (tcgen05 3xTF32, in-kernel split) and
-// 7 (tcgen05 3xTF32, pre-split tiles fed by TMA) exist for FP32 only.
-bool cfg_valid(int cfg, int es, bool tensor) { return cfg < 5 || (tensor && es == 4); }
+// 7 (tcgen05 3xTF32, pre-split tiles fed by TMA) exist for FP32 only; 8 (one
+// warp per 32-128 columns, gemm_small.cu) needs M <= 32 and row-major B and C
+// (skinny = true); 9-11 are the vector-read CUDA-core tiles of gemm_small.cu.
+bool cfg_valid(int cfg, int es, bool tensor, bool skinny) {
+  if (cfg == 8) return skinny;
+  return cfg < 5 || cfg > 8 || (tensor && es == 4);
+}
 
 template <class T>
 void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st, int* err) {
@@ -645,6 +652,10 @@ void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st, int* err
       if constexpr (sizeof(T) == 4) k_gemm_tf32x3<<<grid, 256, 0, st>>>(g);
       else k_gemm<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(g);
       break;
+    case 8:
+    case 9:
+    case 10:
+    case 11: launch_gemm_small<T>(cfg - 8, g, grid, g.batch, (int)grid.z, st); break;
     default:
       if constexpr (sizeof(T) == 4) {
         launch_tc05_any(grid, g, st, err);
@@ -655,7 +666,8 @@ void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st, int* err
   }
 }
 
-int heuristic_cfg(int M, int N, int K, long batch, int es, bool tensor) {
+int heuristic_cfg(int M, int N, int K, long batch, int es, bool tensor, bool skinny) {
+  if (es == 4 && tensor && skinny) return 8;
   if (es == 4 && tensor && M >= 64 && N >= 32) return (M >= 768 && N >= 768 && K >= 2048) ? 7 : 6;
   if (M <= 32 && N <= 32) return 2;
   if (M >= 96 && N >= 96) return es == 4 ? (tensor ? 6 : 4) : 3;
@@ -677,10 +689,17 @@ std::vector<std::pair<unsigned long long, int>> g_tuned;
 // Tuning cache key: element size, tensor-core permission and the log2 classes
 // of the shape (a handle that forbids the tensor cores never reuses a choice
 // made by one that allows them).
-unsigned long long shape_key(int es, bool tensor, int M, int N, int K, long batch) {
+// M, N and K fall in half-octave classes (v in [2^b, 1.5 * 2^b) or [1.5 * 2^b, 2^(b+1))), the batch
+// in octaves; the operand layouts (which stride is 1) and whether the one-warp-per-slab tiling
+// applies (M <= 32, which a class can straddle) are part of the key.
+unsigned long long shape_key(int es, bool tensor, int M, int N, int K, long batch, int layout) {
   auto lg = [](long v) { int b = 0; while (v > 1) { v >>= 1; ++b; } return (unsigned long long)b; };
-  return (unsigned long long)es | (lg(M) << 8) | (lg(N) << 16) | (lg(K) << 24) | (lg(batch) << 32) |
-         ((unsigned long long)(tensor ? 1 : 0) << 48);
+  auto lh = [&](long v) {
+    const unsigned long long b = lg(v);
+    return 2 * b + ((b >= 1 && v >= (3L << (b - 1))) ? 1 : 0);
+  };
+  return (unsigned long long)es | (lh(M) << 8) | (lh(N) << 16) | (lh(K) << 24) | (lg(batch) << 32) |
+         ((unsigned long long)(tensor ? 1 : 0) << 48) | ((unsigned long long)layout << 49);
 }
 
 }  // namespace
@@ -724,6 +743,70 @@ static void run_gemm(Ctx& c, int cfg, int split, int M, int N, int K, long batch
              (double)sizeof(T) * batch * ((double)M * K + (double)K * N + (double)M * N * (1 + (g.beta != T(0)))));
     }
   }
+}
+
+// Debug check (ACR_GEMM_VERIFY=1): the chosen tiling and the reference FMA
+// tiling (0) both compute alpha A B into scratch; the largest difference (upper
+// triangle only for symmetric products) is compared with the reference's
+// magnitude, and non-finite values the reference does not have are reported.
+template <class T>
+__global__ void k_cmp_max(const T* __restrict__ x, const T* __restrict__ y, long tot, int M, int N, int sym,
+                          unsigned* out) {
+  float md = 0.f, mr = 0.f;
+  int bad = 0;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    const long r = e % ((long)M * N);
+    if (sym && r / N > r % N) continue;
+    const T a = x[e], b = y[e];
+    if (!isfinite((double)a) && isfinite((double)b)) bad = 1;
+    md = fmaxf(md, (float)fabs((double)a - (double)b));
+    mr = fmaxf(mr, (float)fabs((double)b));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+    mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, __float_as_uint(md));
+    atomicMax(out + 1, __float_as_uint(mr));
+    if (bad) atomicOr(out + 2, 1u);
+  }
+}
+
+template <class T>
+static void verify_choice(Ctx& c, int cfg, int split, int M, int N, int K, long batch, const GArgs<T>& g) {
+  static int reported = 0;
+  const size_t cn = (size_t)batch * M * N;
+  T* s1 = c.alloc<T>(cn);
+  T* s2 = c.alloc<T>(cn);
+  unsigned* d = c.alloc<unsigned>(4);
+  GArgs<T> gt = g;
+  gt.beta = T(0);
+  gt.C.rs = N; gt.C.cs = 1; gt.C.ps = (long)g.nclus * M * N; gt.C.c1 = (long)M * N;
+  gt.C.c2 = 0; gt.C.sh = 0; gt.C.sib = 0;
+  gt.C.p = s1;
+  run_gemm<T>(c, cfg, split, M, N, K, batch, gt);
+  gt.C.p = s2;
+  run_gemm<T>(c, 0, 1, M, N, K, batch, gt);
+  ACR_CUDA(cudaMemsetAsync(d, 0, 4 * sizeof(unsigned), c.st));
+  k_cmp_max<T><<<(int)std::min<size_t>((cn + 255) / 256, 152 * 16), 256, 0, c.st>>>(s1, s2, (long)cn, M, N,
+                                                                                     g.sym ? 1 : 0, d);
+  unsigned h[4];
+  ACR_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, c.st));
+  ACR_CUDA(cudaStreamSynchronize(c.st));
+  float md, mr;
+  std::memcpy(&md, &h[0], 4);
+  std::memcpy(&mr, &h[1], 4);
+  const float rt = sizeof(T) == 4 ? 1e-3f : 1e-9f;
+  if ((h[2] || !(md <= rt * mr)) && reported < 200) {
+    ++reported;
+    std::fprintf(stderr, "acr gemm verify MISMATCH %s M%d N%d K%d b%ld cfg %d split %d sym %d: max diff %g, max ref %g%s\n",
+                 c.tag, M, N, K, batch, cfg, split, g.sym, md, mr, h[2] ? ", non-finite values" : "");
+  }
+  c.free(d, 4);
+  c.free(s2, cn);
+  c.free(s1, cn);
 }
 
 // Host check of the element range an operand touches over all batch entries.
@@ -772,13 +855,16 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
   if (batch > 0x7fffffffL) throw AcrError(1, "gemm batch too large");
   c.gemm_flops += (sym ? 1LL * M * (N + 1) : 2LL * M * N) * K * batch;
   GArgs<T> g{M, N, K, nclus, (int)batch, alpha, beta, A, B, C, K, nullptr, sym};
-  int cfg = heuristic_cfg(M, N, K, batch, (int)sizeof(T), c.tensor);
+  const bool skinny = M <= 32 && B.cs == 1 && C.cs == 1;
+  int cfg = heuristic_cfg(M, N, K, batch, (int)sizeof(T), c.tensor, skinny);
   int split = split_for(cfg, M, N, K, batch);
-  if (c.force_cfg >= 0 && c.force_cfg < kNCfg && cfg_valid(c.force_cfg, (int)sizeof(T), c.tensor)) {
+  if (c.force_cfg >= 0 && c.force_cfg < kNCfg && cfg_valid(c.force_cfg, (int)sizeof(T), c.tensor, skinny)) {
     cfg = c.force_cfg;
     split = split_for(cfg, M, N, K, batch);
   } else if (c.autotune) {
-    unsigned long long key = shape_key(sizeof(T), c.tensor, M, N, K, batch);
+    const int layout =
+        (A.cs == 1 ? 1 : 0) | (B.cs == 1 ? 2 : 0) | (C.cs == 1 ? 4 : 0) | (sym ? 8 : 0) | (skinny ? 16 : 0);
+    unsigned long long key = shape_key(sizeof(T), c.tensor, M, N, K, batch, layout);
     int found = -1;
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -800,7 +886,7 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
       int bestc = 0;
       for (int cand = 0; cand < 2 * kNCfg; ++cand) {
         int cf = cand % kNCfg;
-        if (!cfg_valid(cf, (int)sizeof(T), c.tensor)) continue;
+        if (!cfg_valid(cf, (int)sizeof(T), c.tensor, skinny)) continue;
         int sp = (cand / kNCfg) ? split_for(cf, M, N, K, batch) : 1;
         if ((cand / kNCfg) && sp == 1) continue;
         run_gemm<T>(c, cf, sp, M, N, K, batch, gt);  // warm
@@ -819,14 +905,18 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tuned.push_back({key, found});
     }
-    cfg = found % kNCfg;
-    split = (found / kNCfg) ? split_for(cfg, M, N, K, batch) : 1;
+    // a class shares one choice; it is valid for every member (the key holds the layouts and skinny)
+    if (cfg_valid(found % kNCfg, (int)sizeof(T), c.tensor, skinny)) {
+      cfg = found % kNCfg;
+      split = (found / kNCfg) ? split_for(cfg, M, N, K, batch) : 1;
+    }
   }
   if (c.profile && c.site_detail) {
     char buf[160];
     std::snprintf(buf, sizeof(buf), "%s M%d N%d K%d b%ld c%d s%d", c.tag, M, N, K, batch, cfg, split);
     c.tag = c.tagstore.insert(buf).first->c_str();
   }
+  if (c.verify_gemm && cfg != 0) verify_choice<T>(c, cfg, split, M, N, K, batch, g);
   run_gemm<T>(c, cfg, split, M, N, K, batch, g);
   if (sym == 1) {
     long tot = batch * (long)M * N;

@@ -297,9 +297,385 @@ __global__ void __launch_bounds__(kQT)
   }
 }
 
+// Register-resident variant (FP32, blocks of at most 512 x 512).  The
+// factorisation is bound by the reflector application, a rank-1 update of
+// every remaining column per pivot step: with the columns in shared memory it
+// streams the whole local matrix through the shared-memory pipe twice per
+// step.  Here warp w of CTA q holds CPW columns (q * 16 * CPW + w * CPW + u)
+// in registers, lane l rows l + 32 t (t < RPL), so the dot products and the
+// update are register FMAs plus one shuffle reduction, and only the
+// reflector (RPL values per lane) is read from shared memory.  Every warp
+// computes, from its registers, the Householder vector of its own best
+// remaining column (speculatively); one cluster barrier publishes the
+// 16 x NC candidates, warp 0 of every CTA reduces them in the same order (same
+// pivot, same stop decision everywhere) and every CTA copies the winner's
+// vector over distributed shared memory.  Candidates and entries alternate
+// between two buffers by step parity, so a CTA writing step st + 1's can never
+// overwrite what another CTA still reads for step st.  Q_k is then formed
+// from the reflectors in the same register layout, the next reflector
+// prefetched into the other half of a double buffer while one is applied.
+template <int RPL, int CPW>
+__global__ void __launch_bounds__(kQT, 1)
+    k_qrcp_reg(int r, int ldv, const float* __restrict__ Call, const int* __restrict__ kk, long NB,
+               float* __restrict__ Vref, float* __restrict__ Xall, float* __restrict__ Yall,
+               float* __restrict__ sigall, int* __restrict__ rankall, float tol, int frob,
+               const float* __restrict__ floor2) {
+  constexpr int NW = kQT / 32;
+  constexpr int CW = NW * CPW;
+  constexpr unsigned FULL = 0xffffffffu;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int NC = (int)cluster.num_blocks();
+  const int q = (int)cluster.block_rank();
+  extern __shared__ float4 smraw4[];
+  float* cand = reinterpret_cast<float*>(smraw4);  // [2][NW][ldv] candidate reflectors
+  float* vloc = cand + 2L * NW * ldv;               // [2][ldv] the chosen reflector
+  float* taus = vloc + 2L * ldv;                    // [ldv]
+  float* sigs = taus + ldv;                         // [ldv]
+  __shared__ float e_best[2][NW], e_sum[2][NW], e_tau[2][NW], e_beta[2][NW];
+  __shared__ int e_idx[2][NW];
+  __shared__ float s_thr2, s_tau, s_beta;
+  __shared__ int s_p, s_src, s_stop;
+  const long bi = blockIdx.x / NC;
+  const float* C = Call + bi * (long)r * r;
+  float* Vb = Vref + bi * (long)r * r;
+  const int kL = kk[bi], kR = kk[NB + bi];
+  const int kmax = min(kL, kR);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c0 = q * CW + warp * CPW;  // this warp's first column
+  float* sig = sigall + bi * r;
+  if (kmax == 0) {  // uniform over the cluster
+    if (q == 0) {
+      if (tid == 0) rankall[bi] = 0;
+      for (int i = tid; i < r; i += blockDim.x) sig[i] = 0.f;
+    }
+    return;
+  }
+  float W[RPL][CPW];
+#pragma unroll
+  for (int t = 0; t < RPL; ++t)
+#pragma unroll
+    for (int u = 0; u < CPW; ++u) {
+      const int row = lane + 32 * t, col = c0 + u;
+      W[t][u] = (row < kL && col < kR) ? C[(long)row * r + col] : 0.f;
+    }
+  // per column (replicated over the lanes): squared remaining norm, its last
+  // exact value, and the step it was chosen at (-1 remaining, -2 absent)
+  float nrm[CPW], nrm0[CPW];
+  int tj[CPW];
+#pragma unroll
+  for (int u = 0; u < CPW; ++u) {
+    float a = 0.f;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) a += W[t][u] * W[t][u];
+    a = wred_sum(a);
+    nrm[u] = a;
+    nrm0[u] = a;
+    tj[u] = (c0 + u < kR) ? -1 : -2;
+  }
+  for (int i = tid; i < 2 * ldv; i += blockDim.x) vloc[i] = 0.f;
+  __syncthreads();
+  int rank = 0;
+  for (int st = 0; st < kmax; ++st) {
+    const int buf = st & 1;
+    const int ts = st >> 5, ls = st & 31;
+    {
+      // the warp's best remaining column and its Householder vector (rows st..kL-1)
+      float best = -1.f, sum = 0.f, tau = 0.f, beta = 0.f;
+      int ub = -1;
+#pragma unroll
+      for (int u = 0; u < CPW; ++u)
+        if (tj[u] == -1) {
+          sum += fmaxf(nrm[u], 0.f);
+          if (nrm[u] > best) { best = nrm[u]; ub = u; }
+        }
+      if (ub >= 0) {
+        float col[RPL];
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          float v = 0.f;
+#pragma unroll
+          for (int u = 0; u < CPW; ++u)
+            if (u == ub) v = W[t][u];
+          col[t] = v;
+        }
+        float x0l = 0.f, xn2 = 0.f;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          const int row = lane + 32 * t;
+          if (t == ts) x0l = col[t];
+          if (row > st) xn2 += col[t] * col[t];
+        }
+        const float x0 = __shfl_sync(FULL, x0l, ls);
+        xn2 = wred_sum(xn2);
+        beta = x0;
+        float scal = 0.f;
+        if (xn2 > 0.f) {
+          beta = -copysignf(sqrtf(x0 * x0 + xn2), x0);
+          tau = (beta - x0) / beta;
+          scal = 1.f / (x0 - beta);
+        }
+        float* cv = cand + ((long)buf * NW + warp) * ldv;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          const int row = lane + 32 * t;
+          if (row > st && row < kL) cv[row] = col[t] * scal;
+        }
+        if (lane == 0) cv[st] = 1.f;
+      }
+      if (lane == 0) {
+        e_best[buf][warp] = best;
+        e_sum[buf][warp] = sum;
+        e_tau[buf][warp] = tau;
+        e_beta[buf][warp] = beta;
+        e_idx[buf][warp] = ub >= 0 ? c0 + ub : 0x7fffffff;
+      }
+    }
+    cluster.sync();
+    if (warp == 0) {
+      // the same reduction over the NC x NW candidates in every CTA
+      float b = -1.f, sm = 0.f, tw = 0.f, bw = 0.f;
+      int bb = 0x7fffffff, src = 0;
+      for (int m = lane; m < NC * NW; m += 32) {
+        const int cta = m / NW, wq = m - cta * NW;
+        const float ob = *cluster.map_shared_rank(&e_best[buf][wq], cta);
+        const int oi = *cluster.map_shared_rank(&e_idx[buf][wq], cta);
+        sm += *cluster.map_shared_rank(&e_sum[buf][wq], cta);
+        if (ob > b || (ob == b && oi < bb)) {
+          b = ob;
+          bb = oi;
+          tw = *cluster.map_shared_rank(&e_tau[buf][wq], cta);
+          bw = *cluster.map_shared_rank(&e_beta[buf][wq], cta);
+          src = m;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(FULL, b, o);
+        const int oi = __shfl_xor_sync(FULL, bb, o);
+        const float ot = __shfl_xor_sync(FULL, tw, o);
+        const float obw = __shfl_xor_sync(FULL, bw, o);
+        const int os = __shfl_xor_sync(FULL, src, o);
+        sm += __shfl_xor_sync(FULL, sm, o);
+        if (ov > b || (ov == b && oi < bb)) { b = ov; bb = oi; tw = ot; bw = obw; src = os; }
+      }
+      if (lane == 0) {
+        if (st == 0) s_thr2 = tol * tol * b;
+        s_p = bb;
+        s_tau = tw;
+        s_beta = bw;
+        s_src = src;
+        s_stop = !((frob ? sm : b) > s_thr2) || !(b > (floor2 ? floor2[bi] : 0.f));
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;  // identical in every CTA of the cluster
+    const int p = s_p;
+    const float tau = s_tau;
+    {
+      const int scta = s_src / NW, swarp = s_src - scta * NW;
+      const float* vs = cand + ((long)buf * NW + swarp) * ldv;
+      const float* vsrc = (scta == q) ? vs : cluster.map_shared_rank(vs, scta);
+      for (int i = st + tid; i < kL; i += blockDim.x) vloc[i] = vsrc[i];
+    }
+    if (tid == 0) {
+      taus[st] = tau;
+      sigs[st] = fabsf(s_beta);
+    }
+    if (p >= c0 && p < c0 + CPW) {
+      // this warp owns p: its column becomes R's column (rows 0..st), its reflector is kept for Q
+      const int up = p - c0;
+#pragma unroll
+      for (int u = 0; u < CPW; ++u)
+        if (u == up) {
+          tj[u] = st;
+#pragma unroll
+          for (int t = 0; t < RPL; ++t) {
+            const int row = lane + 32 * t;
+            if (row == st) W[t][u] = s_beta;
+            else if (row > st) W[t][u] = 0.f;
+          }
+        }
+      const float* vs = cand + ((long)buf * NW + warp) * ldv;
+      for (int i = st + lane; i < kL; i += 32) Vb[(long)st * r + i] = vs[i];
+    }
+    __syncthreads();
+    // apply H = I - tau v v^T to the remaining columns; row st becomes R's row st
+    if (tau != 0.f) {
+      float vr[RPL];
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int row = lane + 32 * t;
+        vr[t] = (row >= st && row < kL) ? vloc[row] : 0.f;
+      }
+      float w[CPW];
+#pragma unroll
+      for (int u = 0; u < CPW; ++u) {
+        float a = 0.f;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) a += vr[t] * W[t][u];
+        w[u] = a;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < CPW; ++u) w[u] += __shfl_xor_sync(FULL, w[u], o);
+#pragma unroll
+      for (int u = 0; u < CPW; ++u) {
+        if (tj[u] != -1) continue;  // uniform over the warp
+        const float f = w[u] * tau;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) W[t][u] -= f * vr[t];
+      }
+    }
+    // downdate the remaining norms by R's row st; recompute one that lost its digits
+#pragma unroll
+    for (int u = 0; u < CPW; ++u) {
+      if (tj[u] != -1) continue;
+      float xl = 0.f;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t)
+        if (t == ts) xl = W[t][u];
+      const float x = __shfl_sync(FULL, xl, ls);
+      float nn = nrm[u] - x * x;
+      if (nn < 0.05f * nrm0[u]) {
+        float a = 0.f;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t)
+          if (lane + 32 * t > st) a += W[t][u] * W[t][u];
+        a = wred_sum(a);
+        nrm0[u] = a;
+        nn = a;
+      }
+      nrm[u] = nn;
+    }
+    rank = st + 1;
+  }
+  cluster.sync();  // every step's reflector rows are in Vb and visible cluster-wide
+  // Y[j][t] = R[t][j] / sig_t for this warp's columns
+  float* Y = Yall + bi * (long)r * r;
+#pragma unroll
+  for (int u = 0; u < CPW; ++u) {
+    if (tj[u] == -2) continue;
+    const int j = c0 + u;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int row = lane + 32 * t;
+      if (row >= rank) continue;
+      const float d = sigs[row];
+      const float val = (tj[u] < 0 || row <= tj[u]) ? W[t][u] : 0.f;
+      Y[(long)j * r + row] = d > 0.f ? val / d : 0.f;
+    }
+  }
+  // Q_k = H_0 ... H_{k-1} [I; 0]: CTA q forms columns t0 .. t0 + nloc - 1, local column
+  // tl in warp tl % NW, slot tl / NW (nloc <= CW since rank <= NC * CW)
+  const int ck = (rank + NC - 1) / NC;
+  const int t0 = q * ck, nloc = max(0, min(rank, t0 + ck) - t0);
+#pragma unroll
+  for (int t = 0; t < RPL; ++t)
+#pragma unroll
+    for (int u = 0; u < CPW; ++u) {
+      const int tl = warp + NW * u;
+      W[t][u] = (tl < nloc && lane + 32 * t == t0 + tl) ? 1.f : 0.f;
+    }
+  int vb = 0;
+  if (rank > 0)
+    for (int i = tid; i < kL; i += blockDim.x) vloc[i] = i >= rank - 1 ? Vb[(long)(rank - 1) * r + i] : 0.f;
+  __syncthreads();
+  for (int tp = rank - 1; tp >= 0; --tp) {
+    if (tp > 0) {
+      float* nx = vloc + (long)(vb ^ 1) * ldv;
+      for (int i = tid; i < kL; i += blockDim.x) nx[i] = i >= tp - 1 ? Vb[(long)(tp - 1) * r + i] : 0.f;
+    }
+    const float tau = taus[tp];
+    if (tau != 0.f && tp < t0 + nloc) {
+      const float* cv = vloc + (long)vb * ldv;
+      float vr[RPL];
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int row = lane + 32 * t;
+        vr[t] = row < kL ? cv[row] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < CPW; ++u) {
+        const int tl = warp + NW * u;
+        if (tl >= nloc || t0 + tl < tp) continue;  // uniform over the warp
+        float a = 0.f;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) a += vr[t] * W[t][u];
+        a = wred_sum(a) * tau;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) W[t][u] -= a * vr[t];
+      }
+    }
+    __syncthreads();
+    vb ^= 1;
+  }
+  float* X = Xall + bi * (long)r * r;
+#pragma unroll
+  for (int u = 0; u < CPW; ++u) {
+    const int tl = warp + NW * u;
+    if (tl >= nloc) continue;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int row = lane + 32 * t;
+      if (row < r) X[(long)row * r + t0 + tl] = row < kL ? W[t][u] : 0.f;
+    }
+    for (int row = 32 * RPL + lane; row < r; row += 32) X[(long)row * r + t0 + tl] = 0.f;
+  }
+  if (q == 0) {
+    for (int i = tid; i < r; i += blockDim.x) sig[i] = i < rank ? sigs[i] : 0.f;
+    if (tid == 0) rankall[bi] = rank;
+  }
+}
+
+template <int RPL, int CPW>
+static bool launch_qrcp_reg(Ctx& c, int r, const float* C, const int* kk, long NB, int kmaxL, int kmaxR, double tol,
+                            int frob, const float* floor2, float* X, float* Y, float* sig, int* rank,
+                            const char* site) {
+  constexpr int CW = (kQT / 32) * CPW;
+  const int NC = (kmaxR + CW - 1) / CW;
+  const int ldv = (kmaxL + 3) / 4 * 4;
+  const size_t sm = (2 * (size_t)(kQT / 32) + 4) * ldv * sizeof(float);
+  if (NC > 8 || kmaxL > 32 * RPL) return false;
+  ACR_CUDA(cudaFuncSetAttribute(k_qrcp_reg<RPL, CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(NB * NC));
+  cfg.blockDim = dim3(kQT);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = c.st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = NC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_qrcp_reg<RPL, CPW>, &cfg) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  DBuf<float> Vref(c, NB * (size_t)r * r);
+  c.kbegin();
+  ACR_CUDA(cudaLaunchKernelEx(&cfg, k_qrcp_reg<RPL, CPW>, r, ldv, C, kk, NB, Vref.p, X, Y, sig, rank, (float)tol,
+                              frob, floor2));
+  c.kend(KC_JACOBI, 0, (double)NB * sizeof(float) * 3.0 * kmaxL * kmaxR, site);
+  return true;
+}
+
 template <class T>
 bool qrcp_cluster(Ctx& c, int r, const T* C, const int* kk, long NB, int kmaxL, int kmaxR, double tol, int frob,
                   const T* floor2, T* X, T* Y, T* sig, int* rank, const char* site) {
+  if constexpr (sizeof(T) == 4) {
+    if (c.qrcp_reg && kmaxL <= 512 && kmaxR <= 512) {
+      const bool ok = kmaxL <= 128   ? launch_qrcp_reg<4, 8>(c, r, C, kk, NB, kmaxL, kmaxR, tol, frob, floor2, X, Y, sig,
+                                                             rank, site)
+                      : kmaxL <= 256 ? launch_qrcp_reg<8, 8>(c, r, C, kk, NB, kmaxL, kmaxR, tol, frob, floor2, X, Y,
+                                                             sig, rank, site)
+                                     : launch_qrcp_reg<16, 4>(c, r, C, kk, NB, kmaxL, kmaxR, tol, frob, floor2, X, Y,
+                                                              sig, rank, site);
+      if (ok) return true;
+    }
+  }
   const size_t cap = 220 * 1024;
   const int ldw = kmaxL | 1;  // odd: the column-major stores of a row run over distinct banks
   // The smallest cluster (<= 8 CTAs) whose CTAs fit several to an SM (each

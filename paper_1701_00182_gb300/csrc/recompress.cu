@@ -913,7 +913,7 @@ __global__ void k_dense_uv(int P, int m, int s, int nclus, int r, int Kout, cons
 template <class T>
 static void truncate_cores(Ctx& c, int r, const T* C, const int* kk, long NB, int kmaxL, int kmaxR, double tol,
                            DBuf<T>& Xo, DBuf<T>& Yo, DBuf<T>& sig, DBuf<int>& rank, const char* site, int frob,
-                           const T* floor2 = nullptr) {
+                           const T* floor2 = nullptr, bool prefer_cluster = false) {
   DBuf<T> W(c, NB * (size_t)r * r);
   Xo = DBuf<T>(c, NB * (size_t)r * r);
   Yo = DBuf<T>(c, NB * (size_t)r * r);
@@ -925,8 +925,12 @@ static void truncate_cores(Ctx& c, int r, const T* C, const int* kk, long NB, in
     base2 = (base2 + 15) / 16 * 16;
     int se2 = (int)std::min<size_t>((size_t)r * r, cap > base2 ? (cap - base2) / sizeof(T) : 0);
     size_t sm2 = base2 + (size_t)se2 * sizeof(T);
-    // Matrices beyond one CTA's shared memory: the cluster kernel keeps them on chip.
-    if ((long)kmaxL * kmaxR > se2 && c.qrcp_cluster &&
+    // Matrices beyond one CTA's shared memory: the cluster kernel keeps them on chip.  In FP32
+    // the register-resident cluster kernel also takes the blocks the caller prefers there
+    // (explicit blocks of 128+ rows; large cores in batches too small to fill the GPU with
+    // one CTA each), where it measured faster than the one-CTA kernel.
+    const bool reg = sizeof(T) == 4 && c.qrcp_reg && (prefer_cluster || c.qrcp_reg_all);
+    if (((long)kmaxL * kmaxR > se2 || reg) && c.qrcp_cluster &&
         qrcp_cluster<T>(c, r, C, kk, NB, kmaxL, kmaxR, tol, frob, floor2, Xo.p, Yo.p, sig.p, rank.p, site))
       return;
     ACR_CUDA(cudaFuncSetAttribute(k_qrcp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
@@ -1014,7 +1018,7 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
     // sigma_1).  FP32: on the largest remaining column -- the Frobenius sum of
     // s rounding-level columns (~u sqrt(s) each) exceeds tol^2 at tol ~1e-6.
     truncate_cores<T>(c, s, Mt.p, kk.p, NB, s, s, tol, Xo, Yo, sig, rank, site_name(c, "qrcp", s, true),
-                      sizeof(T) == 8 ? 1 : 0, fl2.p);
+                      sizeof(T) == 8 ? 1 : 0, fl2.p, s >= 128);
     std::vector<int> hr(NB);
     ACR_CUDA(cudaMemcpyAsync(hr.data(), rank.p, NB * sizeof(int), cudaMemcpyDeviceToHost, c.st));
     ACR_CUDA(cudaStreamSynchronize(c.st));
@@ -1181,7 +1185,8 @@ void recompress_level(Ctx& c, int P, int m, int lvl, DBuf<T>&& Left, DBuf<T>&& R
   }
   DBuf<T> Xo, Yo, sig;
   DBuf<int> rank;
-  truncate_cores<T>(c, r, Cc.p, kk.p, NB, kmaxL, kmaxR, tol, Xo, Yo, sig, rank, site_name(c, "qrcp", s, dens), 0);
+  truncate_cores<T>(c, r, Cc.p, kk.p, NB, kmaxL, kmaxR, tol, Xo, Yo, sig, rank, site_name(c, "qrcp", s, dens), 0,
+                    nullptr, (long)kmaxL * kmaxR >= 128 * 128 && NB <= 512);
   std::vector<int> hr(NB);
   ACR_CUDA(cudaMemcpyAsync(hr.data(), rank.p, NB * sizeof(int), cudaMemcpyDeviceToHost, c.st));
   ACR_CUDA(cudaStreamSynchronize(c.st));

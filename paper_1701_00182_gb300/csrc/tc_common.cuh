@@ -27,6 +27,12 @@ __device__ __forceinline__ T* opaddr(const Op<T>& o, int plane, int c) {
 // FP32 GEMM with pre-split TF32 operand tiles fed by TMA (tma_gemm.cu).
 void gemm_tma(Ctx& c, const GArgs<float>& g, long batch, int split, int* err);
 
+// CUDA-core tilings for small batched products (gemm_small.cu): kind 0 = one
+// warp per column slab (M <= 32, B and C row-major; grid computed inside),
+// 1/2/3 = 64x64 / 64x128 / 128x64 tiles on the grid (batch, tiles, split).
+template <class T>
+void launch_gemm_small(int kind, const GArgs<T>& g, dim3 grid, long batch, int split, cudaStream_t st);
+
 // Every mbarrier wait inside a kernel gives up after this long (ns).
 constexpr unsigned long long kWaitNs = 2000000000ull;
 

@@ -373,6 +373,7 @@ __global__ void __launch_bounds__(kQT, 1)
     tj[u] = (c0 + u < kR) ? -1 : -2;
   }
   for (int i = tid; i < 2 * ldv; i += blockDim.x) vloc[i] = 0.f;
+  const float fl2 = floor2 ? floor2[bi] : 0.f;
   __syncthreads();
   int rank = 0;
   for (int st = 0; st < kmax; ++st) {
@@ -433,20 +434,28 @@ __global__ void __launch_bounds__(kQT, 1)
     cluster.sync();
     if (warp == 0) {
       // the same reduction over the NC x NW candidates in every CTA
+      // all loads of a lane's (at most four) entries are issued before any is used
+      float ob[4], os[4], ot[4], obt[4];
+      int oi[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int m = lane + 32 * e;
+        ob[e] = -1.f; os[e] = 0.f; ot[e] = 0.f; obt[e] = 0.f; oi[e] = 0x7fffffff;
+        if (m < NC * NW) {
+          const int cta = m / NW, wq = m - cta * NW;
+          ob[e] = *cluster.map_shared_rank(&e_best[buf][wq], cta);
+          oi[e] = *cluster.map_shared_rank(&e_idx[buf][wq], cta);
+          os[e] = *cluster.map_shared_rank(&e_sum[buf][wq], cta);
+          ot[e] = *cluster.map_shared_rank(&e_tau[buf][wq], cta);
+          obt[e] = *cluster.map_shared_rank(&e_beta[buf][wq], cta);
+        }
+      }
       float b = -1.f, sm = 0.f, tw = 0.f, bw = 0.f;
       int bb = 0x7fffffff, src = 0;
-      for (int m = lane; m < NC * NW; m += 32) {
-        const int cta = m / NW, wq = m - cta * NW;
-        const float ob = *cluster.map_shared_rank(&e_best[buf][wq], cta);
-        const int oi = *cluster.map_shared_rank(&e_idx[buf][wq], cta);
-        sm += *cluster.map_shared_rank(&e_sum[buf][wq], cta);
-        if (ob > b || (ob == b && oi < bb)) {
-          b = ob;
-          bb = oi;
-          tw = *cluster.map_shared_rank(&e_tau[buf][wq], cta);
-          bw = *cluster.map_shared_rank(&e_beta[buf][wq], cta);
-          src = m;
-        }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        sm += os[e];
+        if (ob[e] > b || (ob[e] == b && oi[e] < bb)) { b = ob[e]; bb = oi[e]; tw = ot[e]; bw = obt[e]; src = lane + 32 * e; }
       }
       for (int o = 16; o > 0; o >>= 1) {
         const float ov = __shfl_xor_sync(FULL, b, o);
@@ -463,7 +472,7 @@ __global__ void __launch_bounds__(kQT, 1)
         s_tau = tw;
         s_beta = bw;
         s_src = src;
-        s_stop = !((frob ? sm : b) > s_thr2) || !(b > (floor2 ? floor2[bi] : 0.f));
+        s_stop = !((frob ? sm : b) > s_thr2) || !(b > fl2);
       }
     }
     __syncthreads();

@@ -258,6 +258,29 @@ const char* acr_error_string(int status);
  */
 int acr_plane_ordering(int n, int leaf, int* perm, int* ncut);
 
+/*
+ * acr_plan_blocks -- host-only query of the block cluster tree of one plane
+ * (Section 2.1: index set, cluster tree, block cluster tree, admissibility
+ * condition).  Clusters are those of acr_plane_ordering; a cluster holds a
+ * rectangle of grid nodes and its geometric region is their convex hull.
+ * Standard admissibility (eta >= 0): a pair of clusters (t, s) of one level
+ * is admissible -- one low-rank block -- when
+ *     min(diam(t), diam(s)) <= eta * dist(t, s),
+ * decided exactly in squared grid steps; otherwise it is split into the four
+ * pairs of children, and pairs of leaves stay dense blocks.  eta < 0 selects
+ * weak admissibility (the HODLR structure acr_factor uses: the two sibling
+ * off-diagonal blocks of every node low rank, the diagonal leaves dense).
+ *   blocks  (host) NULL, or room for `cap` blocks of four ints: level l, row
+ *           cluster t, column cluster s (level-l clusters cover the permuted
+ *           range [t m / 2^l, (t + 1) m / 2^l), m = n^2), and 1 = low rank,
+ *           0 = dense; in depth-first order, row child before column child.
+ *   nblocks (host) receives the number of blocks.
+ * Returns ACR_OK; ACR_ERR_ARG for n or leaf invalid (as acr_plane_ordering),
+ * eta not finite, nblocks NULL, or blocks non-NULL with cap below the count
+ * (*nblocks is still set, nothing is written).  Needs no GPU.
+ */
+int acr_plan_blocks(int n, int leaf, double eta, int* blocks, long cap, long* nblocks);
+
 #ifdef __cplusplus
 }
 #endif

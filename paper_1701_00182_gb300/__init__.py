@@ -121,6 +121,7 @@ def load_library():
         "acr_destroy": (None, [H]),
         "acr_error_string": (C.c_char_p, [C.c_int]),
         "acr_plane_ordering": (C.c_int, [C.c_int, C.c_int, P, P]),
+        "acr_plan_blocks": (C.c_int, [C.c_int, C.c_int, C.c_double, P, C.c_long, C.POINTER(C.c_long)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -366,6 +367,22 @@ def acr_plane_ordering(n: int, leaf: int):
     if L < 0:
         raise AcrError(-L, "acr_plane_ordering")
     return perm, ncut[:L].copy()
+
+
+def acr_plan_blocks(n: int, leaf: int, eta=None):
+    """Host-only planner query: the block cluster tree of one plane as an
+    (nblocks, 4) int array of (level, t, s, low rank); eta None = weak."""
+    lib = load_library()
+    e = -1.0 if eta is None else float(eta)
+    cnt = C.c_long(0)
+    st = lib.acr_plan_blocks(int(n), int(leaf), e, None, 0, C.byref(cnt))
+    if st != ACR_OK:
+        raise AcrError(st, "acr_plan_blocks")
+    out = np.empty((cnt.value, 4), dtype=np.int32)
+    st = lib.acr_plan_blocks(int(n), int(leaf), e, out.ctypes.data, cnt.value, C.byref(cnt))
+    if st != ACR_OK:
+        raise AcrError(st, "acr_plan_blocks")
+    return out
 
 
 def _colmajor(t):

@@ -823,6 +823,24 @@ int acr_plane_ordering(int n, int leaf, int* perm, int* ncut) {
   return g.L;
 }
 
+int acr_plan_blocks(int n, int leaf, double eta, int* blocks, long cap, long* nblocks) {
+  if (!nblocks) return ACR_ERR_ARG;
+  *nblocks = 0;
+  std::vector<std::array<int, 4>> b;
+  try {
+    if (plan_blocks(n, leaf, eta, b)) return ACR_ERR_ARG;
+  } catch (const std::bad_alloc&) {
+    return ACR_ERR_OOM;
+  }
+  *nblocks = (long)b.size();
+  if (blocks) {
+    if (cap < (long)b.size()) return ACR_ERR_ARG;
+    for (size_t i = 0; i < b.size(); ++i)
+      for (int k = 0; k < 4; ++k) blocks[4 * i + k] = b[i][k];
+  }
+  return ACR_OK;
+}
+
 int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_opts* opts, acr_handle* out) {
   if (!out) return ACR_ERR_ARG;
   *out = nullptr;

@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <array>
 #include <map>
 #include <set>
 #include <string>
@@ -200,6 +201,8 @@ struct Geometry {
   std::vector<std::vector<int>> cutp, cutq;  // per level: [node*ncut + e] positions
 };
 int plan_geometry(int n, int leaf, Geometry& g);  // 0 or ACR_ERR_ARG
+// Leaves of the block cluster tree of one plane: (level, t, s, low rank); eta < 0 = weak.
+int plan_blocks(int n, int leaf, double eta, std::vector<std::array<int, 4>>& out);  // 0 or 1 (bad argument)
 
 // ---- small kernels (small_kernels.cu) -------------------------------------
 template <class T> void fill(Ctx& c, T* p, long n, T v);

@@ -8,7 +8,9 @@
 // range of the permuted index.  For every node the grid edges crossing its
 // bisection are enumerated along the cut: they are the exact rank-one terms of
 // the off-diagonal blocks of the 5-point in-plane operator.
+#include <algorithm>
 #include <array>
+#include <cmath>
 #include <vector>
 
 #include "acr_internal.h"
@@ -77,6 +79,71 @@ int plan_geometry(int n, int leaf, Geometry& g) {
       g.cutq[l].insert(g.cutq[l].end(), cq.begin(), cq.end());
     }
     g.ncut[l] = nc;
+  }
+  return 0;
+}
+
+// Block cluster tree of one plane (Section 2.1: index set, cluster tree,
+// block cluster tree, admissibility condition).  Clusters are the rectangles
+// of the bisection tree above; a cluster holds the grid nodes x0 <= i < x1,
+// y0 <= j < y1, whose convex hull is the rectangle with corners (x0, y0) and
+// (x1 - 1, y1 - 1) in grid steps.  Standard admissibility: the pair (t, s) of
+// one level is stored low rank when min(diam t, diam s) <= eta dist(t, s);
+// both sides scale with the grid step, so the test is taken in grid steps and
+// squared (exact integers on the left) -- a cluster is never admissible with
+// itself.  An inadmissible pair is split into the four pairs of its children
+// (row child first, then column child); pairs of leaves stay dense.  eta < 0:
+// weak admissibility (siblings low rank, only diagonal pairs recurse).
+int plan_blocks(int n, int leaf, double eta, std::vector<std::array<int, 4>>& out) {
+  out.clear();
+  if (!std::isfinite(eta)) return 1;
+  Geometry g;
+  if (plan_geometry(n, leaf, g)) return 1;
+  const int L = g.L;
+  using Rect = std::array<int, 4>;
+  std::vector<std::vector<Rect>> rects(L + 1);
+  rects[0].push_back({0, n, 0, n});
+  for (int l = 0; l < L; ++l)
+    for (const Rect& r : rects[l]) {
+      const int w = r[1] - r[0], h = r[3] - r[2];
+      if (w >= h) {
+        const int xm = r[0] + w / 2;
+        rects[l + 1].push_back({r[0], xm, r[2], r[3]});
+        rects[l + 1].push_back({xm, r[1], r[2], r[3]});
+      } else {
+        const int ym = r[2] + h / 2;
+        rects[l + 1].push_back({r[0], r[1], r[2], ym});
+        rects[l + 1].push_back({r[0], r[1], ym, r[3]});
+      }
+    }
+  auto diam2 = [](const Rect& r) -> long {
+    const long a = r[1] - 1 - r[0], b = r[3] - 1 - r[2];
+    return a * a + b * b;
+  };
+  auto dist2 = [](const Rect& a, const Rect& b) -> long {
+    const long dx = std::max({0, b[0] - (a[1] - 1), a[0] - (b[1] - 1)});
+    const long dy = std::max({0, b[2] - (a[3] - 1), a[2] - (b[3] - 1)});
+    return dx * dx + dy * dy;
+  };
+  const bool weak = eta < 0;
+  // explicit stack in the order of the recursion: the children pushed in reverse
+  std::vector<std::array<int, 3>> stack{{0, 0, 0}};
+  while (!stack.empty()) {
+    const auto [l, t, s] = stack.back();
+    stack.pop_back();
+    bool lowrank;
+    if (weak) {
+      lowrank = t != s;
+    } else {
+      const long d2 = dist2(rects[l][t], rects[l][s]);
+      lowrank = d2 > 0 && (double)std::min(diam2(rects[l][t]), diam2(rects[l][s])) <= eta * eta * (double)d2;
+    }
+    if (lowrank || l == L) {
+      out.push_back({l, t, s, lowrank ? 1 : 0});
+      continue;
+    }
+    for (int a = 1; a >= 0; --a)
+      for (int b = 1; b >= 0; --b) stack.push_back({l + 1, 2 * t + a, 2 * s + b});
   }
   return 0;
 }

@@ -30,12 +30,12 @@ from .operator import assemble, plane_blocks
 from .ordering import cluster_tree
 
 
-def _row(label, M, n, leaf, tol, etas):
+def _row(label, M, n, leaf, tol, etas, weak=True):
     perm, _ = cluster_tree(n, leaf)
     P = np.array(perm)
     Mp = M[np.ix_(P, P)]
     out = []
-    for eta in [None] + list(etas):
+    for eta in ([None] if weak else []) + list(etas):
         levels, blocks = adm.block_partition(n, leaf, eta)
         st = adm.storage(adm.compress(Mp, levels, blocks, tol))
         out.append((label, n, leaf, tol, "weak" if eta is None else "eta=%g" % eta, st["words"] * 8 / 2 ** 20,
@@ -43,14 +43,22 @@ def _row(label, M, n, leaf, tol, etas):
     return out
 
 
-def plane_inverse(n: int, leaf: int, tol: float, etas, seed: int = 1):
-    """(a): the inverse of the in-plane block of plane n/2 (GRF kappa)."""
+def plane_inverse(n: int, leaf, tol: float, etas, seed: int = 1, weak_leaf=None):
+    """(a): the inverse of the in-plane block of plane n/2 (GRF kappa), on
+    the partitions of every leaf size in ``leaf`` (the weak partition only for
+    ``weak_leaf``, default the first)."""
     g = synthetic.gaussian_random_field(n, seed)
     A = assemble(n, g).tocsr()
     m = n * n
     k = n // 2
     D = A[k * m:(k + 1) * m, k * m:(k + 1) * m].toarray()
-    return _row("X = inv(D_k), level 0", np.linalg.inv(D), n, leaf, tol, etas)
+    X = np.linalg.inv(D)
+    leaves = [leaf] if isinstance(leaf, int) else list(leaf)
+    wl = leaves[0] if weak_leaf is None else weak_leaf
+    rows = []
+    for lf in leaves:
+        rows += _row("X = inv(D_k), level 0", X, n, lf, tol, etas, weak=(lf == wl))
+    return rows
 
 
 def reduction(n: int, leaf: int, tol: float, etas, seed: int = 1):
@@ -116,7 +124,7 @@ def main():
                    acr_accuracy(32, 32, 1e-4, etas) + acr_accuracy(32, 32, 1e-6, etas))
     elif "--large" in sys.argv:
         # the plane size of Table flopsTable's dense reference (16384^2 FP64 = 2147 MB)
-        _print(plane_inverse(128, 64, 1e-4, etas))
+        _print(plane_inverse(128, (64, 16), 1e-4, etas))
     else:
         _print(plane_inverse(32, 32, 1e-4, etas) + plane_inverse(64, 64, 1e-4, etas) +
                plane_inverse(32, 32, 1e-6, etas) + plane_inverse(64, 64, 1e-6, etas))

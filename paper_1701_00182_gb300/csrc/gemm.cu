@@ -637,6 +637,13 @@ bool cfg_valid(int cfg, int es, bool tensor, bool skinny) {
   return cfg < 5 || cfg > 8 || (tensor && es == 4);
 }
 
+// The tile index of the grid's y dimension stays below its 65535 limit (the
+// one-warp-per-slab tiling puts its slabs on x).
+bool grid_ok(int cfg, int M, int N) {
+  if (cfg == 8) return true;
+  return (long)((M + kCfg[cfg].bm - 1) / kCfg[cfg].bm) * ((N + kCfg[cfg].bn - 1) / kCfg[cfg].bn) <= 65535;
+}
+
 template <class T>
 void launch_cfg(int cfg, dim3 grid, const GArgs<T>& g, cudaStream_t st, int* err) {
   switch (cfg) {
@@ -858,7 +865,8 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
   const bool skinny = M <= 32 && B.cs == 1 && C.cs == 1;
   int cfg = heuristic_cfg(M, N, K, batch, (int)sizeof(T), c.tensor, skinny);
   int split = split_for(cfg, M, N, K, batch);
-  if (c.force_cfg >= 0 && c.force_cfg < kNCfg && cfg_valid(c.force_cfg, (int)sizeof(T), c.tensor, skinny)) {
+  if (c.force_cfg >= 0 && c.force_cfg < kNCfg && cfg_valid(c.force_cfg, (int)sizeof(T), c.tensor, skinny) &&
+      grid_ok(c.force_cfg, M, N)) {
     cfg = c.force_cfg;
     split = split_for(cfg, M, N, K, batch);
   } else if (c.autotune) {
@@ -886,7 +894,7 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
       int bestc = 0;
       for (int cand = 0; cand < 2 * kNCfg; ++cand) {
         int cf = cand % kNCfg;
-        if (!cfg_valid(cf, (int)sizeof(T), c.tensor, skinny)) continue;
+        if (!cfg_valid(cf, (int)sizeof(T), c.tensor, skinny) || !grid_ok(cf, M, N)) continue;
         int sp = (cand / kNCfg) ? split_for(cf, M, N, K, batch) : 1;
         if ((cand / kNCfg) && sp == 1) continue;
         run_gemm<T>(c, cf, sp, M, N, K, batch, gt);  // warm
@@ -906,7 +914,7 @@ static void gemm_impl(Ctx& c, int M, int N, int K, int nplanes, int nclus, T alp
       g_tuned.push_back({key, found});
     }
     // a class shares one choice; it is valid for every member (the key holds the layouts and skinny)
-    if (cfg_valid(found % kNCfg, (int)sizeof(T), c.tensor, skinny)) {
+    if (cfg_valid(found % kNCfg, (int)sizeof(T), c.tensor, skinny) && grid_ok(found % kNCfg, M, N)) {
       cfg = found % kNCfg;
       split = (found / kNCfg) ? split_for(cfg, M, N, K, batch) : 1;
     }

@@ -275,13 +275,15 @@ void launch_gemm_small(int kind, const GArgs<T>& g, dim3 grid, long batch, int s
       if (g.M > 32 || g.B.cs != 1 || (!g.partial && g.C.cs != 1))
         throw AcrError(ACR_ERR_ARG, "one-warp-per-slab GEMM tiling needs M <= 32 and row-major B and C");
       const int mt = g.M <= 8 ? 8 : g.M <= 16 ? 16 : 32;
-      const bool one = g.N <= 32 || (sizeof(T) == 8 && mt == 32);
+      const bool one = g.N <= 32;
       if (mt == 8) {
         if (one) launch_skinny_t<T, 8, 1>(g, batch, split, st);
         else launch_skinny_t<T, 8, 2>(g, batch, split, st);
       } else if (mt == 16) {
         if (one) launch_skinny_t<T, 16, 1>(g, batch, split, st);
         else launch_skinny_t<T, 16, 2>(g, batch, split, st);
+      } else if constexpr (sizeof(T) == 8) {
+        launch_skinny_t<T, 32, 1>(g, batch, split, st);  // two FP64 columns per lane would spill
       } else {
         if (one) launch_skinny_t<T, 32, 1>(g, batch, split, st);
         else launch_skinny_t<T, 32, 2>(g, batch, split, st);

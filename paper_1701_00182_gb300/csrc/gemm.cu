@@ -8,6 +8,7 @@
 // with autotuning enabled the fastest one per (precision, shape class) is
 // measured once with CUDA events and cached for the process.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -812,7 +813,7 @@ __global__ void k_cmp_max(const T* __restrict__ x, const T* __restrict__ y, long
 
 template <class T>
 static void verify_choice(Ctx& c, int cfg, int split, int M, int N, int K, long batch, const GArgs<T>& g) {
-  static int reported = 0;
+  static std::atomic<int> reported{0};
   const size_t cn = (size_t)batch * M * N;
   T* s1 = c.alloc<T>(cn);
   T* s2 = c.alloc<T>(cn);
@@ -835,8 +836,7 @@ static void verify_choice(Ctx& c, int cfg, int split, int M, int N, int K, long 
   std::memcpy(&md, &h[0], 4);
   std::memcpy(&mr, &h[1], 4);
   const float rt = sizeof(T) == 4 ? 1e-3f : 1e-9f;
-  if ((h[2] || !(md <= rt * mr)) && reported < 200) {
-    ++reported;
+  if ((h[2] || !(md <= rt * mr)) && reported.fetch_add(1) < 200) {
     std::fprintf(stderr, "acr gemm verify MISMATCH %s M%d N%d K%d b%ld cfg %d split %d sym %d: max diff %g, max ref %g%s\n",
                  c.tag, M, N, K, batch, cfg, split, g.sym, md, mr, h[2] ? ", non-finite values" : "");
   }

@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libacr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
-SOURCES = ["gemm.cu", "gemm_small.cu", "tma_gemm.cu", "small_kernels.cu", "recompress.cu", "qrcp_cluster.cu", "acr.cu", "noalloc.cu", "coarse.cu", "plan.cpp"]
+SOURCES = ["gemm.cu", "gemm_small.cu", "tma_gemm.cu", "small_kernels.cu", "recompress.cu", "qrcp_cluster.cu", "qrcp_blocked.cu", "acr.cu", "noalloc.cu", "coarse.cu", "plan.cpp"]
 
 
 def _nvcc() -> str:

@@ -874,6 +874,8 @@ int acr_factor(int n, const double* log_kappa, double tol, int leaf, const acr_o
     const char* qr = std::getenv("ACR_QRCP_REG");
     c.qrcp_reg = !(qr && qr[0] == '0');
     c.qrcp_reg_all = qr && qr[0] == '2';
+    const char* qb = std::getenv("ACR_QRCP_BLOCKED");
+    c.qrcp_blocked = qb && qb[0] == '1';
     const char* gv = std::getenv("ACR_GEMM_VERIFY");
     c.verify_gemm = gv && gv[0] == '1';
     const char* sd = std::getenv("ACR_PROFILE_SITES");

@@ -64,6 +64,7 @@ struct Ctx {
   bool qrcp_cluster = true;    // pivoted QR of large cores / explicit blocks on a thread-block cluster
   bool qrcp_reg = true;        // FP32 blocks up to 512 x 512: the register-resident cluster variant (ACR_QRCP_REG=0: off)
   bool qrcp_reg_all = false;   // ACR_QRCP_REG=2: also the blocks that fit one CTA's shared memory
+  bool qrcp_blocked = false;   // ACR_QRCP_BLOCKED=1: several pivots per cluster barrier (not yet run on a GPU)
   int core_svd = 0;           // core truncation: 0 / 2 pivoted QR (default), 1 Jacobi SVD
   void check_range(const void* base, long lo, long hi, size_t es, const char* what) const;
   bool profile = false;  // record CUDA events around every launch, accumulated per kernel class
@@ -250,6 +251,12 @@ template <class S, class D> void convert(Ctx& c, long n, const S* a, D* b);
 template <class T>
 bool qrcp_cluster(Ctx& c, int r, const T* C, const int* kk, long NB, int kmaxL, int kmaxR, double tol, int frob,
                   const T* floor2, T* X, T* Y, T* sig, int* rank, const char* site);
+
+// The same truncation (FP32, blocks up to 512 x 512, column stop criterion)
+// with up to 16 pivots chosen per round of cluster barriers from a sketch of
+// the trailing matrix (qrcp_blocked.cu).  Returns false when it does not apply.
+bool qrcp_blocked(Ctx& c, int r, const float* C, const int* kk, long NB, int kmaxL, int kmaxR, double tol,
+                  const float* floor2, float* X, float* Y, float* sig, int* rank, const char* site);
 
 // ---- recompression (recompress.cu) ----------------------------------------
 // Level-l recompression of the off-diagonal blocks  Left|c * Right|c^1 ^T  for

@@ -675,6 +675,8 @@ template <class T>
 bool qrcp_cluster(Ctx& c, int r, const T* C, const int* kk, long NB, int kmaxL, int kmaxR, double tol, int frob,
                   const T* floor2, T* X, T* Y, T* sig, int* rank, const char* site) {
   if constexpr (sizeof(T) == 4) {
+    if (c.qrcp_blocked && !frob && qrcp_blocked(c, r, C, kk, NB, kmaxL, kmaxR, tol, floor2, X, Y, sig, rank, site))
+      return true;
     if (c.qrcp_reg && kmaxL <= 512 && kmaxR <= 512) {
       const bool ok = kmaxL <= 128   ? launch_qrcp_reg<4, 8>(c, r, C, kk, NB, kmaxL, kmaxR, tol, frob, floor2, X, Y, sig,
                                                              rank, site)
